@@ -1,0 +1,398 @@
+"""Throughput of the two-stage JSON parse on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload config2|config1|config0]
+
+A step is one whole parse (setup, stage 1, stage 2, finalize kernels and the
+result header copy) of one synthetic document that already sits in HBM.  The
+default workload is the 1 GiB single document (records in a root array, ~30%
+non-ASCII string bytes, escape runs across block and tile edges, 1% of records
+nested to depth 1024): larger than L2, so no flush is needed between steps.
+
+`value` is whole-job input GB/s over K steps timed with CUDA events on the
+launching stream (max over ranks).  `e2e` is the same metric through sj_parse
+with a pinned host buffer (host-to-device copy inside every step, result
+header read back).  `roofline` reports the dominant kernel against the
+measured HBM copy bandwidth; `cpu_baseline` times the CPU oracle on a bounded
+sample of the same workload on this host's cores.
+
+--impl reference times the CPU oracle itself (the only reference that exists
+for this workload) on a bounded sample per step.
+
+N > 1 (torchrun): every rank parses its own document of the same size
+(independent replicas, weak scaling); only the timing uses the process group.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "config2": ("1 GiB single document: root array of config-0 style records, ~30% non-ASCII "
+                "string bytes, \\u surrogate pairs, escape runs on 64 B / 2 KiB / 128 KiB edges, "
+                "1% of records nested to depth 1024", 1 << 30),
+    "config1": ("2.5 MB number-heavy single document (polygons of [lon,lat] pairs, 15-17 "
+                "significant digits, minimal white space)", 2_500_000),
+    "config0": ("64 KB record document, 2-space pretty printing", 65536),
+}
+
+
+def make_doc(workload: str, seed: int, size: int | None = None) -> np.ndarray:
+    import gen
+    if workload == "config2":
+        return gen.config2(seed, size=size or (1 << 30))
+    if workload == "config1":
+        return gen.config1(seed)
+    return gen.config0(seed)
+
+
+def record_prefix(doc: np.ndarray, nbytes: int) -> bytes:
+    """The first whole records of a config-2 document, closed into a valid array."""
+    b = doc[: nbytes].tobytes()
+    cut = b.rfind(b"\n  },\n  {")
+    if cut < 0:
+        return doc.tobytes()
+    return b[: cut + 4] + b"\n]\n"
+
+
+def load_peaks() -> dict:
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return {"hbm_gbs": float(d["hbm_gbs"]), "source": "measured"}
+    return {"hbm_gbs": 6800.0, "source": "fallback"}
+
+
+def source_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1902_08318_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            with open(os.path.join(csrc, name), "rb") as f:
+                h.update(name.encode() + f.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic(kernel: str):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel sources."""
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    if d.get("source_hash") != source_hash():
+        return None
+    ent = d.get("kernels", {}).get(kernel)
+    if not ent or "bytes_per_launch_full_size" not in ent:
+        return None
+    return ent["bytes_per_launch_full_size"]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self):
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, ValueError):
+            self.proc = None
+
+    def stop(self, gpu_index: int = 0) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                if int(parts[0]) != gpu_index:
+                    continue
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def lexeme_bytes(doc_dev, idx_dev) -> int:
+    """Input bytes of the string, number and atom lexemes (read by stage 2)."""
+    import torch
+    x = doc_dev
+    n = idx_dev.numel()
+    pos = idx_dev.to(torch.int64)
+    first = x[pos]
+    is_val = (first == ord('"')) | (first == ord("t")) | (first == ord("f")) | (first == ord("n")) | \
+        (first == ord("-")) | ((first >= ord("0")) & (first <= ord("9")))
+    nxt = torch.empty_like(pos)
+    nxt[:-1] = pos[1:]
+    nxt[-1] = x.numel()
+    q = (nxt - 1)[is_val]
+    p0 = pos[is_val]
+    for _ in range(64):  # step back over white space before the next token
+        c = x[q]
+        ws = (c == 32) | (c == 9) | (c == 10) | (c == 13)
+        if not bool(ws.any()):
+            break
+        q = q - ws.to(torch.int64)
+    del n
+    return int((q - p0 + 1).sum().item())
+
+
+def run_ours(args, rank: int, world: int, dist) -> dict | None:
+    import torch
+
+    import paper_1902_08318_gb300 as sj
+
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    desc, size = WORKLOADS[args.workload]
+    doc = make_doc(args.workload, 2000 + rank)
+    B = int(doc.size)
+    doc_dev = torch.from_numpy(doc).to(dev)
+    parser = sj.Parser(max_bytes=B + 64)
+    stream = torch.cuda.current_stream()
+
+    # correctness gate on the benchmarked input (error code only; the
+    # element-by-element parity lives in the gpu tests)
+    r = parser.parse(doc_dev, stream=stream)
+    if r.error != 0:
+        raise SystemExit(f"benchmark document rejected: {r.error_name}")
+    S, T, SB = r.n_indices, r.tape_words, r.string_bytes
+    lex = lexeme_bytes(doc_dev, r.indices()[: S])
+
+    # ---- device-timed region ------------------------------------------------
+    parser.set_profiling(True)
+    for _ in range(args.warmup):
+        parser.parse_async(doc_dev, stream=stream)
+    parser.parse_wait()
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    clocks = ClockSampler()
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    stage_sum = {k: 0.0 for k in sj.STAGES}
+    e0.record(stream)
+    for _ in range(args.steps):
+        parser.parse_async(doc_dev, stream=stream)
+        for k, v in parser.stage_times().items():  # waits for this step
+            stage_sum[k] += v
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop(dev.index)
+    ms_total = e0.elapsed_time(e1)
+    res = parser.parse_wait() if False else None
+    del res
+    if dist:
+        t = torch.tensor([ms_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / args.steps
+    stage_ms = {k: v / args.steps for k, v in stage_sum.items()}
+
+    # ---- end to end through sj_parse from pinned host memory ------------------
+    parser.set_profiling(False)
+    host = torch.from_numpy(doc).pin_memory()
+    for _ in range(max(1, args.warmup // 2)):
+        parser.parse(host, stream=stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    f0.record(stream)
+    e2e_steps = max(1, min(args.steps, 10))
+    for _ in range(e2e_steps):
+        rr = parser.parse(host, stream=stream)
+        assert rr.error == 0
+    f1.record(stream)
+    torch.cuda.synchronize()
+    ms_e2e = f0.elapsed_time(f1)
+    if dist:
+        t = torch.tensor([ms_e2e], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    if rank != 0:
+        return None
+    peaks = load_peaks()
+    gbs = world * B / (ms_step * 1e-3) / 1e9
+    e2e = world * B / (ms_e2e / e2e_steps * 1e-3) / 1e9
+    algo_path = B + 4 * S + 8 * T + SB
+    algo = {"stage1": B + 4 * S, "stage2": 4 * S + lex + 8 * T + SB}
+    dom = max(("stage1", "stage2"), key=lambda k: stage_ms[k])
+    achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
+    out = {
+        "metric": "parse GB/s (input bytes, device-timed)",
+        "value": round(gbs, 2),
+        "unit": "GB/s",
+        "n_gpus": world,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "bytes_per_doc": B,
+                   "indices": S, "tape_words": T, "string_bytes": SB, "lexeme_bytes": lex,
+                   "l2": "inputs larger than L2 (no flush)" if B > 129e6 else "L2 not flushed",
+                   "parallelism": f"replicas x{world}"},
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": round(achieved / peaks["hbm_gbs"], 4),
+                     "traffic": traffic, "algorithmic_bytes": algo[dom],
+                     "peak_source": peaks["source"]},
+        "path_roofline": {"algorithmic_bytes": algo_path,
+                          "achieved": round(algo_path / (ms_step * 1e-3) / 1e9, 1),
+                          "frac": round(algo_path / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                          "input_frac": round(B / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
+        "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
+        "e2e": {"value": round(e2e, 3), "unit": "GB/s", "h2d_bytes_per_step": B,
+                "d2h_bytes_per_step": 56},
+        "gpu_launches": 4 * args.steps,
+        "clocks": clk,
+    }
+    return out
+
+
+def oracle_gbs(sample: bytes, repeats: int = 1) -> tuple[float, float]:
+    import oracle
+    oracle.parse(sample[:1024])  # build + warm
+    t0 = time.perf_counter()
+    for _ in range(repeats):
+        r = oracle.parse(sample)
+    dt = time.perf_counter() - t0
+    assert r["error"] == 0, r["error"]
+    return len(sample) * repeats / dt / 1e9, dt
+
+
+def cpu_baseline(args) -> dict:
+    sample_bytes = 512 << 20 if args.workload == "config2" else None
+    if args.workload == "config2":
+        doc = make_doc("config2", 2000, size=sample_bytes + (1 << 20))
+        sample = record_prefix(doc, sample_bytes)
+        what = f"first whole records ({len(sample)} bytes) of a config-2 document, single-threaded"
+    else:
+        sample = make_doc(args.workload, 1000 if args.workload == "config1" else 0).tobytes()
+        what = f"the whole {args.workload} document ({len(sample)} bytes), single-threaded"
+    gbs, dt = oracle_gbs(sample)
+    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": what, "seconds": round(dt, 2), "host_cores": os.cpu_count()}
+
+
+def run_reference(args, rank: int) -> dict | None:
+    if rank != 0:
+        return None
+    desc, _ = WORKLOADS[args.workload]
+    if args.workload == "config2":
+        doc = make_doc("config2", 2000, size=(32 << 20) + (1 << 20))
+        sample = record_prefix(doc, 32 << 20)
+        what = f"first whole records ({len(sample)} bytes) of a config-2 document per step"
+    else:
+        sample = make_doc(args.workload, 1000 if args.workload == "config1" else 0).tobytes()
+        what = f"the whole {args.workload} document per step"
+    import oracle
+    oracle.parse(sample[:1024])
+    for _ in range(args.warmup):
+        oracle.parse(sample)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r = oracle.parse(sample)
+        assert r["error"] == 0
+    dt = time.perf_counter() - t0
+    gbs = len(sample) * args.steps / dt / 1e9
+    return {
+        "impl": "reference",
+        "metric": "parse GB/s (input bytes, device-timed)",
+        "value": round(gbs, 4), "unit": "GB/s", "n_gpus": args.gpus, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(dt / args.steps * 1e3, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": f"{args.workload}: {desc}", "bytes_per_step": len(sample)},
+        "cpu_baseline": {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+                         "sample": what},
+        "e2e": {"value": round(gbs, 4), "unit": "GB/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    dist = None
+    if args.impl == "reference":
+        out = run_reference(args, rank)
+        if out:
+            print(json.dumps(out), flush=True)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        tdist.init_process_group("nccl")
+        dist = tdist
+    import __graft_entry__
+    if rank == 0:
+        __graft_entry__.build()
+    if dist:
+        dist.barrier()
+    out = run_ours(args, rank, world, dist)
+    if out is not None:
+        if not args.no_cpu_baseline:
+            out["cpu_baseline"] = cpu_baseline(args)
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

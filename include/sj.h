@@ -1,0 +1,160 @@
+/*
+ * sj.h -- C ABI of a GB300 (sm_103a) implementation of the two-stage
+ * validating JSON parser of "Parsing Gigabytes of JSON per Second"
+ * (G. Langdale, D. Lemire).
+ *
+ * The problem statement (Sec. 3): bytes in; a tape of 64-bit words, a string
+ * buffer and an error code out; the input is never modified.  Stage 1 (Sec.
+ * 3.1) validates UTF-8 and flattens the structural and pseudo-structural
+ * characters into a u32 index array; stage 2 (Sec. 3.2) builds the tape.
+ *
+ * Conventions shared by every call
+ *  - All compute runs in CUDA kernels on the current device; there is no CPU
+ *    fallback.  A call returns an sj_status (below).  A document's own parse
+ *    result (valid or which error) is reported separately, in sj_result.error
+ *    or sj_doc_result.error, as an sj_error code.
+ *  - Input bytes may live in host or device memory (detected with
+ *    cudaPointerGetAttributes).  They are read-only and need no padding.
+ *    Host input, and device input that is not 16-byte aligned, is first copied
+ *    into a parser-owned device buffer.
+ *  - Outputs live in parser-owned device buffers and stay valid until the next
+ *    call on the same parser.  The caller never frees them.
+ *  - A parser is not thread-safe; use one parser per host thread.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).
+ *  - No C++ exception, abort or exit crosses this boundary.
+ *
+ * Output layout (Sec. 3, Fig. "jsontape"; Sec. 3.2.2)
+ *  - indices: u32 byte positions (relative to the document start) of the
+ *    structural and pseudo-structural characters, ascending.
+ *  - tape: u64 words, tag in bits 56..63 and a 56-bit payload.  Word 0 is
+ *    'r' with payload T-1, word T-1 is 'r' with payload 0.  '{'/'[' carry one
+ *    plus the index of the matching closer, '}'/']' the index of the opener.
+ *    '"' carries the byte offset of the string in the string buffer.  'l' and
+ *    'd' are followed by one word: a two's-complement int64, or the binary64
+ *    bits of a correctly rounded double.  't', 'f', 'n' have payload 0.
+ *  - strings: per string, in tape order, a u32 little-endian length, the
+ *    UTF-8 bytes (escapes resolved, may contain NUL), and one NUL byte.
+ */
+#ifndef SJ_H
+#define SJ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Per-document parse result.  Names follow the paper's examples
+ * (STRING_ERROR, NUMBER_ERROR, UTF8_ERROR, Sec. 3); the paper leaves the rest
+ * of the set open ("etc."), this is the full set used here.  When several
+ * problems exist the reported one is, in order: CAPACITY / EMPTY, UTF8_ERROR
+ * (whole input, Sec. 3.1.5), UNCLOSED_STRING (end of stage 1), then the first
+ * failing token in document order, with the grammar checked before the
+ * token's content. */
+typedef enum {
+  SJ_SUCCESS = 0,
+  SJ_CAPACITY = 1,         /* document too large (>= 2^32 - 256 bytes, or above max_bytes) */
+  SJ_MEMALLOC = 2,
+  SJ_TAPE_ERROR = 3,       /* grammar: misplaced token, unbalanced brackets, trailing content */
+  SJ_DEPTH_ERROR = 4,      /* nesting deeper than max_depth */
+  SJ_STRING_ERROR = 5,     /* bad escape or lone UTF-16 surrogate */
+  SJ_T_ATOM_ERROR = 6,
+  SJ_F_ATOM_ERROR = 7,
+  SJ_N_ATOM_ERROR = 8,
+  SJ_NUMBER_ERROR = 9,     /* grammar, int64 range, or a double that overflows */
+  SJ_UTF8_ERROR = 10,
+  SJ_UNCLOSED_STRING = 11,
+  SJ_UNESCAPED_CHARS = 12, /* raw byte < 0x20 inside a string */
+  SJ_EMPTY = 13,           /* no byte other than white space */
+  SJ_INVALID_ARG = 14,
+  SJ_INTERNAL = 15         /* a bounded wait gave up; should not happen */
+} sj_error;
+
+/* Status of a call (as opposed to the document result): SJ_SUCCESS,
+ * SJ_INVALID_ARG, SJ_CAPACITY (input larger than the parser was created for),
+ * SJ_MEMALLOC (a CUDA allocation failed) or SJ_INTERNAL (a CUDA runtime error;
+ * sj_last_cuda_error() tells which). */
+typedef int sj_status;
+
+typedef struct sj_parser sj_parser;
+
+/* Result of sj_parse.  Pointers are device pointers into parser-owned memory. */
+typedef struct {
+  int32_t error;            /* sj_error of the document */
+  uint32_t reserved;
+  uint64_t n_indices;       /* valid unless error is UTF8_ERROR, CAPACITY or EMPTY */
+  uint64_t tape_words;      /* valid when error == SJ_SUCCESS */
+  uint64_t string_bytes;    /* valid when error == SJ_SUCCESS */
+  const uint32_t *indices;
+  const uint64_t *tape;
+  const uint8_t *strings;
+} sj_result;
+
+/* Per-document result of sj_parse_batch (host array, one per document).
+ * Offsets are element offsets into the batch's indices / tape / strings
+ * arrays; payloads inside a document's tape are relative to its own strings. */
+typedef struct {
+  int32_t error;
+  uint32_t reserved;
+  uint64_t n_indices;
+  uint64_t tape_words;
+  uint64_t string_bytes;
+  uint64_t indices_offset;
+  uint64_t tape_offset;
+  uint64_t strings_offset;
+} sj_doc_result;
+
+/* Create a parser for inputs of at most max_bytes bytes in total (summed over
+ * a batch) and at most max_docs documents per batch (0 = 1).  max_depth is
+ * the nesting limit (0 = 4096; at most 4096); the root container has depth 1.
+ * Allocates all device memory up front (about 22 bytes per input byte).
+ * Returns SJ_SUCCESS and *out, or an error status and *out = NULL. */
+sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint32_t max_docs,
+                           uint32_t max_depth);
+
+/* Free a parser and all its device memory.  NULL is ignored. */
+void sj_parser_destroy(sj_parser *p);
+
+/* Parse one document of len bytes and wait for it (stream-synchronous).
+ * The paper's sj_parse(bytes, len): fills *out and returns SJ_SUCCESS, or an
+ * error status (then *out is untouched). */
+sj_status sj_parse(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream,
+                   sj_result *out);
+
+/* As sj_parse but does not wait: the kernels and a copy of the small result
+ * header are queued on `stream`; call sj_parse_wait() before reading *out. */
+sj_status sj_parse_async(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream);
+sj_status sj_parse_wait(sj_parser *p, sj_result *out);
+
+/* Parse n_docs independent documents in one graph-launched set of kernels.
+ * Document i is bytes[doc_offsets[i] .. doc_offsets[i+1]); doc_offsets is a
+ * host array of n_docs+1 non-decreasing values.  Carries reset at every
+ * document start.  out is a host array of n_docs results.  The three device
+ * pointers give the batch output arrays (may be NULL).  Synchronous. */
+sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc_offsets,
+                         uint32_t n_docs, void *stream, sj_doc_result *out,
+                         const uint32_t **indices, const uint64_t **tape,
+                         const uint8_t **strings);
+
+/* Per-kernel timing.  With profiling on, runs launch their kernels directly
+ * (not through the captured graph) with CUDA events recorded between them on
+ * the caller's stream.  sj_parser_stage_times waits for the last run and
+ * writes the durations in milliseconds of its setup, stage-1, stage-2 and
+ * finalize kernels to ms[0..3]. */
+sj_status sj_parser_set_profiling(sj_parser *p, int enable);
+sj_status sj_parser_stage_times(sj_parser *p, float ms[4]);
+
+/* Name of an sj_error code ("SUCCESS", "TAPE_ERROR", ...). */
+const char *sj_error_name(int code);
+
+/* Last CUDA runtime error code seen by the library on this thread (0 = none). */
+int sj_last_cuda_error(void);
+
+/* Library version string. */
+const char *sj_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SJ_H */

@@ -1,0 +1,282 @@
+"""GB300 (sm_103a) two-stage validating JSON parser -- Python binding.
+
+Thin ctypes marshalling over the C ABI declared in include/sj.h; every step of
+the parse runs in the CUDA kernels of csrc/.  PyTorch supplies device memory
+and streams.  There is no CPU fallback: if the CUDA library is missing or no
+GPU is present, calls raise.
+
+    import paper_1902_08318_gb300 as sj
+    p = sj.Parser(max_bytes=1 << 20)
+    r = p.parse(torch_uint8_tensor_or_bytes)
+    r.error, r.indices(), r.tape(), r.strings()
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_ROOT = os.path.dirname(_HERE)
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libsj.so")
+_SOURCES = ["api.cu", "stage1.cu", "stage2.cu"]
+_HEADERS = ["sj_internal.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
+NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
+              "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
+
+ERROR_NAMES = ["SUCCESS", "CAPACITY", "MEMALLOC", "TAPE_ERROR", "DEPTH_ERROR", "STRING_ERROR",
+               "T_ATOM_ERROR", "F_ATOM_ERROR", "N_ATOM_ERROR", "NUMBER_ERROR", "UTF8_ERROR",
+               "UNCLOSED_STRING", "UNESCAPED_CHARS", "EMPTY", "INVALID_ARG", "INTERNAL"]
+globals().update({name: code for code, name in enumerate(ERROR_NAMES)})
+
+_lock = threading.Lock()
+_lib = None
+
+
+def _nvcc() -> str:
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile csrc/*.cu for sm_103a into _build/libsj.so (in-tree)."""
+    srcs = [os.path.join(_CSRC, s) for s in _SOURCES]
+    deps = srcs + [os.path.join(_CSRC, h) for h in _HEADERS] + [os.path.join(_ROOT, "include", "sj.h")]
+    with _lock:
+        if (not force and os.path.exists(LIB_PATH)
+                and os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(d) for d in deps)):
+            return LIB_PATH
+        os.makedirs(_BUILD, exist_ok=True)
+        inc = ["-I", os.path.join(_ROOT, "include"), "-I", _CSRC]
+
+        def compile_one(src):
+            obj = os.path.join(_BUILD, os.path.basename(src) + ".o")
+            cmd = [_nvcc(), *NVCC_FLAGS, *inc, "-c", src, "-o", obj]
+            if verbose:
+                print(" ".join(cmd))
+            subprocess.check_call(cmd)
+            return obj
+
+        with ThreadPoolExecutor(len(srcs)) as ex:
+            objs = list(ex.map(compile_one, srcs))
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.check_call([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                               "-o", tmp, *objs, "-lcudart"])
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class _DocResult(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("n_indices", ctypes.c_uint64), ("tape_words", ctypes.c_uint64),
+                ("string_bytes", ctypes.c_uint64), ("indices_offset", ctypes.c_uint64),
+                ("tape_offset", ctypes.c_uint64), ("strings_offset", ctypes.c_uint64)]
+
+
+class _Result(ctypes.Structure):
+    _fields_ = [("error", ctypes.c_int32), ("reserved", ctypes.c_uint32),
+                ("n_indices", ctypes.c_uint64), ("tape_words", ctypes.c_uint64),
+                ("string_bytes", ctypes.c_uint64), ("indices", ctypes.c_void_p),
+                ("tape", ctypes.c_void_p), ("strings", ctypes.c_void_p)]
+
+
+DOC_RESULT_DTYPE = np.dtype([("error", np.int32), ("reserved", np.uint32),
+                             ("n_indices", np.uint64), ("tape_words", np.uint64),
+                             ("string_bytes", np.uint64), ("indices_offset", np.uint64),
+                             ("tape_offset", np.uint64), ("strings_offset", np.uint64)])
+
+
+def load(path: str | None = None):
+    """Load the CUDA library (no compile).  Raises if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
+    lib.sj_parser_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
+    lib.sj_parser_create.restype = ctypes.c_int
+    lib.sj_parser_destroy.argtypes = [vp]
+    lib.sj_parser_destroy.restype = None
+    lib.sj_parse.argtypes = [vp, vp, u64, vp, ctypes.POINTER(_Result)]
+    lib.sj_parse.restype = ctypes.c_int
+    lib.sj_parse_async.argtypes = [vp, vp, u64, vp]
+    lib.sj_parse_async.restype = ctypes.c_int
+    lib.sj_parse_wait.argtypes = [vp, ctypes.POINTER(_Result)]
+    lib.sj_parse_wait.restype = ctypes.c_int
+    lib.sj_parse_batch.argtypes = [vp, vp, vp, u32, vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                   ctypes.POINTER(vp)]
+    lib.sj_parse_batch.restype = ctypes.c_int
+    lib.sj_parser_set_profiling.argtypes = [vp, ctypes.c_int]
+    lib.sj_parser_set_profiling.restype = ctypes.c_int
+    lib.sj_parser_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.sj_parser_stage_times.restype = ctypes.c_int
+    lib.sj_error_name.argtypes = [ctypes.c_int]
+    lib.sj_error_name.restype = ctypes.c_char_p
+    lib.sj_last_cuda_error.argtypes = []
+    lib.sj_last_cuda_error.restype = ctypes.c_int
+    lib.sj_version.argtypes = []
+    lib.sj_version.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async", "sj_parse_wait",
+            "sj_parse_batch", "sj_parser_set_profiling", "sj_parser_stage_times", "sj_error_name",
+            "sj_last_cuda_error", "sj_version"]
+STAGES = ("setup", "stage1", "stage2", "finalize")
+
+
+class SJError(RuntimeError):
+    pass
+
+
+def _check(status: int):
+    if status != 0:
+        lib = load()
+        raise SJError(f"sj call failed: {ERROR_NAMES[status] if status < 16 else status}"
+                      f" (cuda error {lib.sj_last_cuda_error()})")
+
+
+class _DeviceView:
+    """__cuda_array_interface__ over parser-owned device memory (no copy)."""
+
+    def __init__(self, ptr: int, n: int, typestr: str):
+        self.__cuda_array_interface__ = {"shape": (int(n),), "typestr": typestr,
+                                         "data": (int(ptr), False), "version": 3, "strides": None}
+
+
+def _device_tensor(ptr: int, n: int, typestr: str):
+    import torch
+    return torch.as_tensor(_DeviceView(ptr, n, typestr), device="cuda")
+
+
+def _as_input(data):
+    """(pointer, length, keepalive) of a torch tensor (device or host), numpy array or bytes."""
+    try:
+        import torch
+        if isinstance(data, torch.Tensor):
+            t = data.contiguous()
+            if t.dtype != torch.uint8:
+                t = t.view(torch.uint8)
+            return t.data_ptr(), t.numel(), t
+    except ImportError:
+        pass
+    if isinstance(data, (bytes, bytearray, memoryview)):
+        a = np.frombuffer(bytes(data), dtype=np.uint8)
+    else:
+        a = np.ascontiguousarray(data, dtype=np.uint8)
+    return a.ctypes.data, a.size, a
+
+
+def _stream_handle(stream) -> int:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return int(getattr(stream, "cuda_stream", stream))
+
+
+class Result:
+    """One document's result.  Accessors return device tensors (views)."""
+
+    def __init__(self, error, n_indices, tape_words, string_bytes, idx_ptr, tape_ptr, str_ptr):
+        self.error = int(error)
+        self.error_name = ERROR_NAMES[self.error]
+        self.n_indices = int(n_indices)
+        self.tape_words = int(tape_words)
+        self.string_bytes = int(string_bytes)
+        self._p = (idx_ptr, tape_ptr, str_ptr)
+
+    def indices(self):
+        return _device_tensor(self._p[0], self.n_indices, "<u4")
+
+    def tape(self):
+        return _device_tensor(self._p[1], self.tape_words, "<u8")
+
+    def strings(self):
+        return _device_tensor(self._p[2], self.string_bytes, "|u1")
+
+
+class Parser:
+    """A parser owning device buffers for inputs up to max_bytes (summed over a
+    batch) and max_docs documents per batch."""
+
+    def __init__(self, max_bytes: int, max_docs: int = 1, max_depth: int = 0):
+        import torch
+        if not torch.cuda.is_available():
+            raise SJError("no CUDA device: the parser has no CPU path")
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.sj_parser_create(ctypes.byref(h), int(max_bytes), int(max_docs),
+                                          int(max_depth)))
+        self._h = h
+        self.max_bytes = int(max_bytes)
+        self.max_docs = int(max_docs)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sj_parser_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def parse(self, data, stream=None) -> Result:
+        ptr, n, keep = _as_input(data)
+        r = _Result()
+        _check(self._lib.sj_parse(self._h, ptr, n, _stream_handle(stream), ctypes.byref(r)))
+        del keep
+        return Result(r.error, r.n_indices, r.tape_words, r.string_bytes, r.indices, r.tape,
+                      r.strings)
+
+    def parse_async(self, data, stream=None):
+        ptr, n, keep = _as_input(data)
+        _check(self._lib.sj_parse_async(self._h, ptr, n, _stream_handle(stream)))
+        return keep
+
+    def parse_wait(self) -> Result:
+        r = _Result()
+        _check(self._lib.sj_parse_wait(self._h, ctypes.byref(r)))
+        return Result(r.error, r.n_indices, r.tape_words, r.string_bytes, r.indices, r.tape,
+                      r.strings)
+
+    def parse_batch(self, data, offsets, stream=None):
+        """Returns (results: structured numpy array, indices, tape, strings device tensors
+        covering the batch output arrays)."""
+        ptr, n, keep = _as_input(data)
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        nd = off.size - 1
+        out = np.zeros(nd, dtype=DOC_RESULT_DTYPE)
+        pi, pt, ps = ctypes.c_void_p(), ctypes.c_void_p(), ctypes.c_void_p()
+        _check(self._lib.sj_parse_batch(self._h, ptr, off.ctypes.data, nd, _stream_handle(stream),
+                                        out.ctypes.data, ctypes.byref(pi), ctypes.byref(pt),
+                                        ctypes.byref(ps)))
+        del keep
+        return out, (pi.value, pt.value, ps.value)
+
+    def set_profiling(self, on: bool):
+        _check(self._lib.sj_parser_set_profiling(self._h, int(bool(on))))
+
+    def stage_times(self) -> dict:
+        """Kernel durations (ms) of the last run, measured with CUDA events on
+        its stream (profiling must be on)."""
+        ms = (ctypes.c_float * 4)()
+        _check(self._lib.sj_parser_stage_times(self._h, ms))
+        return dict(zip(STAGES, [float(x) for x in ms]))
+
+    @staticmethod
+    def view(ptr: int, n: int, typestr: str):
+        return _device_tensor(ptr, n, typestr)

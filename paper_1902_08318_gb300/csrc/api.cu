@@ -1,0 +1,389 @@
+// api.cu -- the C ABI of include/sj.h: parser objects, launches, results.
+//
+// A run is five kernels on one stream: setup (tiles per document), stage 1,
+// stage 2, finalize (per-document results; clears the look-back words for the
+// next run), bracketed by a host-to-device copy of the run descriptor and the
+// document offsets and a device-to-host copy of the results.  The sequence is
+// captured once per (parser, document count) as a CUDA graph and replayed.
+#include <cuda_runtime.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <new>
+
+#include "sj_internal.cuh"
+
+namespace sj {
+__global__ void setup_kernel(const Job *job);
+__global__ void stage1_kernel(const Job *job);
+__global__ void stage2_kernel(const Job *job);
+__global__ void finalize_kernel(const Job *job);
+}  // namespace sj
+
+using sj::Job;
+
+static thread_local int g_last_cuda_error = 0;
+
+struct sj_parser {
+  int device = 0;
+  uint64_t max_bytes = 0;
+  uint32_t max_docs = 0;
+  uint32_t max_depth = 0;
+  uint64_t max_tiles = 0;
+  // device memory
+  uint8_t *d_input = nullptr;
+  uint64_t *d_doc_off = nullptr;
+  uint32_t *d_tile_first = nullptr;
+  uint32_t *d_counters = nullptr;
+  uint32_t *d_s1_state = nullptr;
+  uint64_t *d_s1_count = nullptr;
+  uint32_t *d_tile_cnt = nullptr;
+  uint32_t *d_tile_off = nullptr;
+  sj::S2Tile *d_s2 = nullptr;
+  uint32_t *d_s2_flag = nullptr;
+  uint32_t *d_surv = nullptr;
+  uint32_t *d_idx = nullptr;
+  uint64_t *d_tape = nullptr;
+  uint8_t *d_strings = nullptr;
+  uint32_t *d_doc_flags = nullptr;
+  uint32_t *d_doc_nidx = nullptr;
+  unsigned long long *d_doc_err = nullptr;
+  uint64_t *d_doc_tape = nullptr;
+  uint64_t *d_doc_str = nullptr;
+  sj_doc_result *d_results = nullptr;
+  Job *d_job = nullptr;
+  // pinned host memory
+  Job *h_job = nullptr;
+  uint64_t *h_doc_off = nullptr;
+  sj_doc_result *h_results = nullptr;
+  // launch shapes
+  int s1_grid = 0, s2_grid = 0, fin_grid = 0;
+  // graph cache
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t graph = nullptr;
+  uint32_t graph_docs = 0;
+  cudaEvent_t done = nullptr;
+  cudaEvent_t prof[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  bool profiling = false;
+  bool profiled_run = false;
+  bool pending = false;  // an async parse is in flight
+  uint32_t last_docs = 0;
+  uint64_t last_len = 0;
+};
+
+static int cuda_fail(cudaError_t e) {
+  g_last_cuda_error = (int)e;
+  return e == cudaErrorMemoryAllocation ? SJ_MEMALLOC : SJ_INTERNAL;
+}
+#define CK(x)                                   \
+  do {                                          \
+    cudaError_t e_ = (x);                       \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+template <class T>
+static int dalloc(T **p, uint64_t n) {
+  CK(cudaMalloc((void **)p, (size_t)(n ? n : 1) * sizeof(T)));
+  return SJ_SUCCESS;
+}
+
+extern "C" void sj_parser_destroy(sj_parser *p) {
+  if (!p) return;
+  if (p->pending) cudaEventSynchronize(p->done);
+  if (p->graph) cudaGraphExecDestroy(p->graph);
+  if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->done) cudaEventDestroy(p->done);
+  for (cudaEvent_t e : p->prof)
+    if (e) cudaEventDestroy(e);
+  void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_s1_state,
+                 p->d_s1_count, p->d_tile_cnt, p->d_tile_off, p->d_s2, p->d_s2_flag, p->d_surv,
+                 p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
+                 p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job};
+  for (void *q : dev)
+    if (q) cudaFree(q);
+  if (p->h_job) cudaFreeHost(p->h_job);
+  if (p->h_doc_off) cudaFreeHost(p->h_doc_off);
+  if (p->h_results) cudaFreeHost(p->h_results);
+  delete p;
+}
+
+static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint32_t max_depth) {
+  CK(cudaGetDevice(&p->device));
+  p->max_bytes = max_bytes;
+  p->max_docs = max_docs;
+  p->max_depth = max_depth;
+  p->max_tiles = max_bytes / sj::kTileBytes + (uint64_t)max_docs + 1;
+  const uint64_t tiles = p->max_tiles;
+  int r;
+  if ((r = dalloc(&p->d_input, max_bytes + 64))) return r;
+  if ((r = dalloc(&p->d_doc_off, (uint64_t)max_docs + 1))) return r;
+  if ((r = dalloc(&p->d_tile_first, (uint64_t)max_docs + 1))) return r;
+  if ((r = dalloc(&p->d_counters, 4))) return r;
+  if ((r = dalloc(&p->d_s1_state, tiles))) return r;
+  if ((r = dalloc(&p->d_s1_count, tiles))) return r;
+  if ((r = dalloc(&p->d_tile_cnt, tiles))) return r;
+  if ((r = dalloc(&p->d_tile_off, tiles))) return r;
+  if ((r = dalloc(&p->d_s2, tiles))) return r;
+  if ((r = dalloc(&p->d_s2_flag, tiles))) return r;
+  if ((r = dalloc(&p->d_surv, max_bytes + 16))) return r;
+  if ((r = dalloc(&p->d_idx, max_bytes + 16))) return r;
+  if ((r = dalloc(&p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
+  if ((r = dalloc(&p->d_strings, (5 * max_bytes) / 2 + 8ull * max_docs + 64))) return r;
+  if ((r = dalloc(&p->d_doc_flags, max_docs))) return r;
+  if ((r = dalloc(&p->d_doc_nidx, max_docs))) return r;
+  if ((r = dalloc(&p->d_doc_err, max_docs))) return r;
+  if ((r = dalloc(&p->d_doc_tape, max_docs))) return r;
+  if ((r = dalloc(&p->d_doc_str, max_docs))) return r;
+  if ((r = dalloc(&p->d_results, max_docs))) return r;
+  if ((r = dalloc(&p->d_job, 1))) return r;
+  CK(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t)));
+  CK(cudaMemset(p->d_s1_state, 0, tiles * sizeof(uint32_t)));
+  CK(cudaMemset(p->d_s1_count, 0, tiles * sizeof(uint64_t)));
+  CK(cudaMemset(p->d_s2_flag, 0, tiles * sizeof(uint32_t)));
+  CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
+  CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
+  CK(cudaMallocHost((void **)&p->h_results, (size_t)max_docs * sizeof(sj_doc_result)));
+  CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
+  for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
+
+  int sms = 0, occ1 = 0, occ2 = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_kernel, 32 * sj::kS1Warps, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sj::stage2_kernel, sj::kS2Threads, 0));
+  p->s1_grid = sms * (occ1 > 0 ? occ1 : 1);
+  p->s2_grid = sms * (occ2 > 0 ? occ2 : 1);
+  p->fin_grid = sms * 4;
+
+  Job &J = *p->h_job;
+  memset(&J, 0, sizeof(J));
+  J.doc_off = p->d_doc_off;
+  J.max_depth = max_depth;
+  J.max_doc_len = sj::kMaxDocBytes;
+  J.tile_first = p->d_tile_first;
+  J.counters = p->d_counters;
+  J.s1_state = p->d_s1_state;
+  J.s1_count = p->d_s1_count;
+  J.tile_cnt = p->d_tile_cnt;
+  J.tile_off = p->d_tile_off;
+  J.s2 = p->d_s2;
+  J.s2_flag = p->d_s2_flag;
+  J.surv = p->d_surv;
+  J.idx = p->d_idx;
+  J.tape = p->d_tape;
+  J.strings = p->d_strings;
+  J.doc_flags = p->d_doc_flags;
+  J.doc_nidx = p->d_doc_nidx;
+  J.doc_err = p->d_doc_err;
+  J.doc_tape = p->d_doc_tape;
+  J.doc_str = p->d_doc_str;
+  J.results = p->d_results;
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint32_t max_docs,
+                                      uint32_t max_depth) {
+  if (!out) return SJ_INVALID_ARG;
+  *out = nullptr;
+  if (max_docs == 0) max_docs = 1;
+  if (max_depth == 0) max_depth = 4096;
+  if (max_depth > sj::kMaxDepthLimit || max_bytes == 0) return SJ_INVALID_ARG;
+  sj_parser *p = new (std::nothrow) sj_parser();
+  if (!p) return SJ_MEMALLOC;
+  int r = create_impl(p, max_bytes, max_docs, max_depth);
+  if (r) {
+    sj_parser_destroy(p);
+    return r;
+  }
+  *out = p;
+  return SJ_SUCCESS;
+}
+
+// Capture (once per document count) the launch sequence of one run.
+static int ensure_graph(sj_parser *p, uint32_t n_docs) {
+  if (p->graph && p->graph_docs == n_docs) return SJ_SUCCESS;
+  if (p->graph) {
+    cudaGraphExecDestroy(p->graph);
+    p->graph = nullptr;
+  }
+  cudaStream_t s = p->cap_stream;
+  cudaGraph_t g = nullptr;
+  CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+  cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s);
+  cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
+                  cudaMemcpyHostToDevice, s);
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  sj::stage1_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  sj::stage2_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
+                  cudaMemcpyDeviceToHost, s);
+  cudaError_t e = cudaStreamEndCapture(s, &g);
+  if (e != cudaSuccess) return cuda_fail(e);
+  e = cudaGraphInstantiate(&p->graph, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    p->graph = nullptr;
+    return cuda_fail(e);
+  }
+  p->graph_docs = n_docs;
+  return SJ_SUCCESS;
+}
+
+static bool is_device_ptr(const void *ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+static int wait_pending(sj_parser *p) {
+  if (!p->pending) return SJ_SUCCESS;
+  p->pending = false;
+  CK(cudaEventSynchronize(p->done));
+  return SJ_SUCCESS;
+}
+
+// Queue one run over n_docs documents whose offsets are in h_doc_off.
+static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n_docs,
+                  cudaStream_t stream) {
+  int r;
+  if ((r = wait_pending(p))) return r;
+  const uint8_t *base = bytes;
+  if (!is_device_ptr(bytes)) {
+    CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
+    base = p->d_input;
+  }
+  p->h_job->base = base;
+  p->h_job->n_docs = n_docs;
+  if (p->profiling) {
+    // the same sequence as the graph, with events between the kernels
+    CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, stream));
+    CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
+                       cudaMemcpyHostToDevice, stream));
+    CK(cudaEventRecord(p->prof[0], stream));
+    sj::setup_kernel<<<1, 1024, 0, stream>>>(p->d_job);
+    CK(cudaEventRecord(p->prof[1], stream));
+    sj::stage1_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, stream>>>(p->d_job);
+    CK(cudaEventRecord(p->prof[2], stream));
+    sj::stage2_kernel<<<p->s2_grid, sj::kS2Threads, 0, stream>>>(p->d_job);
+    CK(cudaEventRecord(p->prof[3], stream));
+    sj::finalize_kernel<<<p->fin_grid, 256, 0, stream>>>(p->d_job);
+    CK(cudaEventRecord(p->prof[4], stream));
+    CK(cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
+                       cudaMemcpyDeviceToHost, stream));
+    CK(cudaGetLastError());
+    p->profiled_run = true;
+  } else {
+    if ((r = ensure_graph(p, n_docs))) return r;
+    CK(cudaGraphLaunch(p->graph, stream));
+    p->profiled_run = false;
+  }
+  CK(cudaEventRecord(p->done, stream));
+  p->pending = true;
+  p->last_docs = n_docs;
+  return SJ_SUCCESS;
+}
+
+static void fill_result(sj_parser *p, sj_result *out) {
+  const sj_doc_result &r = p->h_results[0];
+  out->error = r.error;
+  out->reserved = 0;
+  out->n_indices = r.n_indices;
+  out->tape_words = r.tape_words;
+  out->string_bytes = r.string_bytes;
+  out->indices = p->d_idx;
+  out->tape = p->d_tape;
+  out->strings = p->d_strings;
+}
+
+extern "C" sj_status sj_parse_async(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream) {
+  if (!p || (!bytes && len)) return SJ_INVALID_ARG;
+  if (len > p->max_bytes) return SJ_CAPACITY;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  p->h_doc_off[0] = 0;
+  p->h_doc_off[1] = len;
+  p->last_len = len;
+  static const uint8_t empty[16] = {0};
+  return launch(p, len ? bytes : empty, len, 1, (cudaStream_t)stream);
+}
+
+extern "C" sj_status sj_parse_wait(sj_parser *p, sj_result *out) {
+  if (!p || !out) return SJ_INVALID_ARG;
+  if (!p->pending) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  CK(cudaGetLastError());
+  fill_result(p, out);
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parse(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream,
+                              sj_result *out) {
+  if (!out) return SJ_INVALID_ARG;
+  int r = sj_parse_async(p, bytes, len, stream);
+  if (r) return r;
+  return sj_parse_wait(p, out);
+}
+
+extern "C" sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc_offsets,
+                                    uint32_t n_docs, void *stream, sj_doc_result *out,
+                                    const uint32_t **indices, const uint64_t **tape,
+                                    const uint8_t **strings) {
+  if (!p || !doc_offsets || !out || n_docs == 0) return SJ_INVALID_ARG;
+  if (n_docs > p->max_docs) return SJ_CAPACITY;
+  for (uint32_t i = 0; i < n_docs; i++)
+    if (doc_offsets[i + 1] < doc_offsets[i]) return SJ_INVALID_ARG;
+  const uint64_t total = doc_offsets[n_docs] - doc_offsets[0];
+  if (total > p->max_bytes) return SJ_CAPACITY;
+  if (!bytes && total) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  const bool dev = total ? is_device_ptr(bytes) : false;
+  // documents are addressed relative to the first one
+  for (uint32_t i = 0; i <= n_docs; i++) p->h_doc_off[i] = doc_offsets[i] - doc_offsets[0];
+  const uint8_t *first = bytes ? bytes + doc_offsets[0] : nullptr;
+  static const uint8_t empty[16] = {0};
+  if (!total) first = empty;
+  (void)dev;
+  if ((r = launch(p, first, total, n_docs, (cudaStream_t)stream))) return r;
+  if ((r = wait_pending(p))) return r;
+  CK(cudaGetLastError());
+  memcpy(out, p->h_results, (size_t)n_docs * sizeof(sj_doc_result));
+  if (indices) *indices = p->d_idx;
+  if (tape) *tape = p->d_tape;
+  if (strings) *strings = p->d_strings;
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parser_set_profiling(sj_parser *p, int enable) {
+  if (!p) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  p->profiling = enable != 0;
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parser_stage_times(sj_parser *p, float ms[4]) {
+  if (!p || !ms) return SJ_INVALID_ARG;
+  if (!p->profiled_run) return SJ_INVALID_ARG;
+  CK(cudaEventSynchronize(p->prof[4]));
+  for (int i = 0; i < 4; i++) CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+  return SJ_SUCCESS;
+}
+
+extern "C" const char *sj_error_name(int code) {
+  static const char *names[] = {"SUCCESS",        "CAPACITY",     "MEMALLOC",     "TAPE_ERROR",
+                                "DEPTH_ERROR",    "STRING_ERROR", "T_ATOM_ERROR", "F_ATOM_ERROR",
+                                "N_ATOM_ERROR",   "NUMBER_ERROR", "UTF8_ERROR",   "UNCLOSED_STRING",
+                                "UNESCAPED_CHARS", "EMPTY",       "INVALID_ARG",  "INTERNAL"};
+  if (code < 0 || code > 15) return "UNKNOWN";
+  return names[code];
+}
+
+extern "C" int sj_last_cuda_error(void) { return g_last_cuda_error; }
+
+extern "C" const char *sj_version(void) { return "sj-gb300 0.1 (sm_103a)"; }

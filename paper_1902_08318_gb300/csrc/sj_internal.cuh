@@ -1,0 +1,149 @@
+// sj_internal.cuh -- shared definitions of the CUDA kernels (device side).
+#pragma once
+#include <stdint.h>
+
+#include "sj.h"
+
+namespace sj {
+
+// Stage 1 (Sec. 3.1) works on 64-byte blocks as in the paper: one block per
+// lane, one warp per tile of 32 blocks.  Stage 2 (Sec. 3.2) processes the
+// indices of one stage-1 tile per thread block.
+constexpr int kBlockBytes = 64;
+constexpr int kTileBytes = 32 * kBlockBytes;  // 2048
+constexpr int kS1Warps = 4;                   // tiles (warps) per stage-1 thread block
+constexpr int kS2Threads = 128;               // threads per stage-2 thread block
+constexpr int kMaxTileTokens = kTileBytes;    // at most one index per byte
+constexpr uint32_t kMaxDepthLimit = 4096;
+constexpr uint64_t kMaxDocBytes = 0xFFFFFF00ull;  // keeps positions and tape indices in u32
+constexpr uint32_t kSpinLimit = 1u << 24;         // bounded waits (polls) in look-back loops
+
+// Per-document flags written by the kernels.
+constexpr uint32_t kFlagUtf8 = 1, kFlagUnclosed = 2, kFlagInternal = 4, kFlagCapacity = 8;
+
+// Look-back status values (top two bits of a status word).
+constexpr uint32_t kStAgg = 1, kStIncl = 2;
+
+// Per-tile record of the stage-2 look-back (Sec. 3.2 state carried between
+// tiles: nesting depth, tape slots, string-buffer bytes).
+struct S2Tile {
+  // aggregate of the tile alone (published with kStAgg)
+  int32_t d_delta;     // depth change over the tile
+  int32_t min_rel;     // lowest depth reached, relative to the tile start (<= 0)
+  uint32_t words;      // tape words written by the tile's tokens
+  uint32_t pad0;
+  uint64_t strbytes;   // string-buffer bytes of the tile's strings
+  // inclusive prefix (published with kStIncl)
+  int32_t d_start;     // absolute depth before the tile's first token
+  uint32_t jump;       // nearest earlier tile of the document with a lower `low`, or kNoTile
+  uint32_t tape_start; // tape index of the tile's first word (document relative)
+  uint32_t pad1;
+  uint64_t str_start;  // string-buffer offset of the tile's first string (document relative)
+};
+constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+// Everything a run needs, in device memory (one copy per parser; refreshed
+// by a host-to-device copy before each run so that one captured graph serves
+// every call).
+struct Job {
+  const uint8_t *base;      // 16-byte aligned buffer holding the documents
+  const uint64_t *doc_off;  // n_docs + 1 byte offsets into base
+  uint32_t n_docs;
+  uint32_t max_depth;
+  uint64_t max_doc_len;
+  // scratch
+  uint32_t *tile_first;     // n_docs + 1: first stage-1 tile of each document
+  uint32_t *counters;       // [0] stage-1 ticket, [1] stage-2 ticket, [2] number of tiles
+  uint32_t *s1_state;       // per tile: escape/quote/separator look-back word
+  uint64_t *s1_count;       // per tile: index-count look-back word
+  uint32_t *tile_cnt;       // per tile: indices produced
+  uint32_t *tile_off;       // per tile: document-relative offset of its first index
+  S2Tile *s2;               // per tile
+  uint32_t *s2_flag;        // per tile
+  uint32_t *surv;           // per index slot: open containers left by a tile (by level)
+  // outputs
+  uint32_t *idx;
+  uint64_t *tape;
+  uint8_t *strings;
+  uint32_t *doc_flags;
+  uint32_t *doc_nidx;
+  unsigned long long *doc_err;  // min over (token << 8 | code)
+  uint64_t *doc_tape;
+  uint64_t *doc_str;
+  sj_doc_result *results;
+};
+
+// Output placement: each document gets capacity proportional to its length.
+__device__ __forceinline__ uint64_t rel_off(const Job &J, uint32_t d) {
+  return J.doc_off[d] - J.doc_off[0];
+}
+__device__ __forceinline__ uint64_t idx_base(const Job &J, uint32_t d) { return rel_off(J, d); }
+__device__ __forceinline__ uint64_t tape_base(const Job &J, uint32_t d) {
+  return rel_off(J, d) + 3ull * d;
+}
+__device__ __forceinline__ uint64_t str_base(const Job &J, uint32_t d) {
+  return (5ull * rel_off(J, d)) / 2 + 8ull * d;
+}
+
+// Document owning global tile t (tile_first is non-decreasing).
+__device__ __forceinline__ uint32_t doc_of_tile(const Job &J, uint32_t t) {
+  uint32_t lo = 0, hi = J.n_docs;  // answer in [lo, hi)
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (J.tile_first[mid] <= t) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// ---- memory-ordering helpers for the decoupled look-back ----------------
+__device__ __forceinline__ uint32_t ld_acquire(const uint32_t *p) {
+  uint32_t v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t ld_acquire(const uint64_t *p) {
+  uint64_t v;
+  asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(uint32_t *p, uint32_t v) {
+  asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release(uint64_t *p, uint64_t v) {
+  asm volatile("st.release.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// ---- token kinds (first byte of an index, Sec. 3.2) ----------------------
+enum : uint8_t {
+  K_OTHER = 0, K_OPEN_OBJ = 1, K_OPEN_ARR = 2, K_CLOSE_OBJ = 3, K_CLOSE_ARR = 4,
+  K_COMMA = 5, K_COLON = 6, K_STRING = 7, K_NUMBER = 8, K_TRUE = 9, K_FALSE = 10, K_NULL = 11
+};
+
+__device__ __forceinline__ uint8_t token_kind(uint8_t c) {
+  switch (c) {
+    case '{': return K_OPEN_OBJ;
+    case '[': return K_OPEN_ARR;
+    case '}': return K_CLOSE_OBJ;
+    case ']': return K_CLOSE_ARR;
+    case ',': return K_COMMA;
+    case ':': return K_COLON;
+    case '"': return K_STRING;
+    case 't': return K_TRUE;
+    case 'f': return K_FALSE;
+    case 'n': return K_NULL;
+    default: return (c == '-' || (uint8_t)(c - '0') < 10) ? K_NUMBER : K_OTHER;
+  }
+}
+__device__ __forceinline__ bool is_open(uint8_t k) { return k == K_OPEN_OBJ || k == K_OPEN_ARR; }
+__device__ __forceinline__ bool is_close(uint8_t k) { return k == K_CLOSE_OBJ || k == K_CLOSE_ARR; }
+__device__ __forceinline__ bool is_atom(uint8_t k) { return k >= K_TRUE && k <= K_NULL; }
+// A token that can start a value.
+__device__ __forceinline__ bool is_value_start(uint8_t k) {
+  return is_open(k) || k == K_STRING || k == K_NUMBER || is_atom(k);
+}
+__device__ __forceinline__ int depth_delta(uint8_t k) { return is_open(k) ? 1 : (is_close(k) ? -1 : 0); }
+__device__ __forceinline__ uint32_t tape_words_of(uint8_t k) {
+  return k == K_NUMBER ? 2u : ((is_open(k) || is_close(k) || k == K_STRING || is_atom(k)) ? 1u : 0u);
+}
+
+}  // namespace sj
