@@ -145,6 +145,21 @@ sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc
 sj_status sj_parser_set_profiling(sj_parser *p, int enable);
 sj_status sj_parser_stage_times(sj_parser *p, float ms[4]);
 
+/* Stage 1 only (structural indices) of one document, allocating nothing.
+ * The paper has no counterpart: this entry exists for callers that cannot call
+ * cudaMalloc when they parse (device memory owned by another allocator, or a
+ * thread that must not trigger cudaMalloc's implicit synchronisation).  The
+ * caller passes device buffers: d_bytes (len bytes, read-only), d_indices
+ * (room for len u32 positions) and d_result (2 u32: the index count, then
+ * flags 1 = invalid UTF-8, 2 = unclosed string, 4 = internal).  The kernel's
+ * scratch is one static device array sized for len <= 64 MiB, held by every GPU
+ * that loads the library until exit; larger inputs return SJ_CAPACITY.  The
+ * first call on a device looks up that array's device address (set-up); make
+ * it before any stream capture.  Calls share the array: calls that overlap on
+ * the GPU race and must be serialised.  Queued on `stream`, not waited for. */
+sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t len, uint32_t *d_indices,
+                                    uint32_t *d_result, void *stream);
+
 /* Name of an sj_error code ("SUCCESS", "TAPE_ERROR", ...). */
 const char *sj_error_name(int code);
 

@@ -25,7 +25,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsj.so")
-_SOURCES = ["api.cu", "stage1.cu", "stage2.cu"]
+_SOURCES = ["api.cu", "stage1.cu", "stage2.cu", "noalloc.cu"]
 _HEADERS = ["sj_internal.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
@@ -121,6 +121,8 @@ def load(path: str | None = None):
     lib.sj_parser_set_profiling.restype = ctypes.c_int
     lib.sj_parser_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
     lib.sj_parser_stage_times.restype = ctypes.c_int
+    lib.sj_stage1_indices_noalloc.argtypes = [vp, u64, vp, vp, vp]
+    lib.sj_stage1_indices_noalloc.restype = ctypes.c_int
     lib.sj_error_name.argtypes = [ctypes.c_int]
     lib.sj_error_name.restype = ctypes.c_char_p
     lib.sj_last_cuda_error.argtypes = []
@@ -132,8 +134,8 @@ def load(path: str | None = None):
 
 
 EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async", "sj_parse_wait",
-            "sj_parse_batch", "sj_parser_set_profiling", "sj_parser_stage_times", "sj_error_name",
-            "sj_last_cuda_error", "sj_version"]
+            "sj_parse_batch", "sj_parser_set_profiling", "sj_parser_stage_times",
+            "sj_stage1_indices_noalloc", "sj_error_name", "sj_last_cuda_error", "sj_version"]
 STAGES = ("setup", "stage1", "stage2", "finalize")
 
 

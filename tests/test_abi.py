@@ -11,7 +11,7 @@ from tests.conftest import ROOT
 def _declared():
     text = open(os.path.join(ROOT, "include", "sj.h")).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(sj_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(sj_[a-z0-9_]+)\s*\(", text)))
 
 
 def test_header_declares_the_boundary():
