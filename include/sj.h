@@ -140,10 +140,14 @@ sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc
 /* Per-kernel timing.  With profiling on, runs launch their kernels directly
  * (not through the captured graph) with CUDA events recorded between them on
  * the caller's stream.  sj_parser_stage_times waits for the last run and
- * writes the durations in milliseconds of its setup, stage-1, stage-2 and
- * finalize kernels to ms[0..3]. */
+ * writes, in milliseconds, the durations of its 8 stages to ms[0..7]: setup,
+ * stage-1 blocks, stage-1 tile scan, stage-1 flatten, stage-2 reduce, stage-2
+ * tile scan and frontier, stage-2 build, finalize.  n must be at least 8. */
 sj_status sj_parser_set_profiling(sj_parser *p, int enable);
-sj_status sj_parser_stage_times(sj_parser *p, float ms[4]);
+sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
+
+/* Number of kernel launches in one run of this parser. */
+int sj_parser_kernels_per_run(const sj_parser *p);
 
 /* Stage 1 only (structural indices) of one document, allocating nothing.
  * The paper has no counterpart: this entry exists for callers that cannot call

@@ -25,8 +25,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsj.so")
-_SOURCES = ["api.cu", "stage1.cu", "stage2.cu", "noalloc.cu"]
-_HEADERS = ["sj_internal.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
+_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu"]
+_HEADERS = ["sj_internal.cuh", "s1_common.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
 
@@ -119,8 +119,10 @@ def load(path: str | None = None):
     lib.sj_parse_batch.restype = ctypes.c_int
     lib.sj_parser_set_profiling.argtypes = [vp, ctypes.c_int]
     lib.sj_parser_set_profiling.restype = ctypes.c_int
-    lib.sj_parser_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float)]
+    lib.sj_parser_stage_times.argtypes = [vp, ctypes.POINTER(ctypes.c_float), ctypes.c_int]
     lib.sj_parser_stage_times.restype = ctypes.c_int
+    lib.sj_parser_kernels_per_run.argtypes = [vp]
+    lib.sj_parser_kernels_per_run.restype = ctypes.c_int
     lib.sj_stage1_indices_noalloc.argtypes = [vp, u64, vp, vp, vp]
     lib.sj_stage1_indices_noalloc.restype = ctypes.c_int
     lib.sj_error_name.argtypes = [ctypes.c_int]
@@ -135,8 +137,10 @@ def load(path: str | None = None):
 
 EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async", "sj_parse_wait",
             "sj_parse_batch", "sj_parser_set_profiling", "sj_parser_stage_times",
-            "sj_stage1_indices_noalloc", "sj_error_name", "sj_last_cuda_error", "sj_version"]
-STAGES = ("setup", "stage1", "stage2", "finalize")
+            "sj_parser_kernels_per_run", "sj_stage1_indices_noalloc", "sj_error_name",
+            "sj_last_cuda_error", "sj_version"]
+STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
+          "s2_build", "finalize")
 
 
 class SJError(RuntimeError):
@@ -275,9 +279,12 @@ class Parser:
     def stage_times(self) -> dict:
         """Kernel durations (ms) of the last run, measured with CUDA events on
         its stream (profiling must be on)."""
-        ms = (ctypes.c_float * 4)()
-        _check(self._lib.sj_parser_stage_times(self._h, ms))
+        ms = (ctypes.c_float * len(STAGES))()
+        _check(self._lib.sj_parser_stage_times(self._h, ms, len(STAGES)))
         return dict(zip(STAGES, [float(x) for x in ms]))
+
+    def kernels_per_run(self) -> int:
+        return int(self._lib.sj_parser_kernels_per_run(self._h))
 
     @staticmethod
     def view(ptr: int, n: int, typestr: str):

@@ -1,10 +1,11 @@
 // api.cu -- the C ABI of include/sj.h: parser objects, launches, results.
 //
-// A run is five kernels on one stream: setup (tiles per document), stage 1,
-// stage 2, finalize (per-document results; clears the look-back words for the
-// next run), bracketed by a host-to-device copy of the run descriptor and the
-// document offsets and a device-to-host copy of the results.  The sequence is
-// captured once per (parser, document count) as a CUDA graph and replayed.
+// A run is a fixed sequence of kernels on one stream (see enqueue_run):
+// setup (tiles per document), stage 1 (blocks, tile scan, flatten), stage 2
+// (reduce, tile scan, frontier, build) and finalize (per-document results),
+// bracketed by a host-to-device copy of the run descriptor and the document
+// offsets and a device-to-host copy of the results.  The sequence is captured
+// once per (parser, document count) as a CUDA graph and replayed.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -15,9 +16,16 @@
 
 namespace sj {
 __global__ void setup_kernel(const Job *job);
-__global__ void stage1_kernel(const Job *job);
-__global__ void stage2_kernel(const Job *job);
+__global__ void stage1_blocks_kernel(const Job *job);
+__global__ void stage1_flatten_kernel(const Job *job);
+__global__ void stage2_reduce_kernel(const Job *job);
+__global__ void stage2_build_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
+__global__ void spt_build_kernel(const Job *job, uint32_t src);
+__global__ void jump_kernel(const Job *job);
+__global__ void frontier_kernel(const Job *job);
+void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
+void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
 }  // namespace sj
 
 using sj::Job;
@@ -35,12 +43,18 @@ struct sj_parser {
   uint64_t *d_doc_off = nullptr;
   uint32_t *d_tile_first = nullptr;
   uint32_t *d_counters = nullptr;
-  uint32_t *d_s1_state = nullptr;
-  uint64_t *d_s1_count = nullptr;
   uint32_t *d_tile_cnt = nullptr;
   uint32_t *d_tile_off = nullptr;
-  sj::S2Tile *d_s2 = nullptr;
-  uint32_t *d_s2_flag = nullptr;
+  sj::S1Agg *d_s1_rec = nullptr;
+  sj::S1Pre *d_s1_pre = nullptr;
+  uint64_t *d_s1_blk = nullptr;
+  sj::S2Agg *d_s2_rec = nullptr;
+  sj::S2Pre *d_s2_pre = nullptr;
+  sj::S2Agg *d_scan_agg = nullptr;
+  sj::S2Agg *d_scan_pre = nullptr;
+  int32_t *d_spt = nullptr;
+  uint32_t *d_slen = nullptr;
+  uint64_t *d_front = nullptr;
   uint32_t *d_surv = nullptr;
   uint32_t *d_idx = nullptr;
   uint64_t *d_tape = nullptr;
@@ -57,13 +71,15 @@ struct sj_parser {
   uint64_t *h_doc_off = nullptr;
   sj_doc_result *h_results = nullptr;
   // launch shapes
-  int s1_grid = 0, s2_grid = 0, fin_grid = 0;
+  int s1_grid = 0, s2_grid = 0, fin_grid = 0, aux_grid = 0;
+  uint32_t scan_blocks = 0, spt_levels = 0;
   // graph cache
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graph = nullptr;
   uint32_t graph_docs = 0;
   cudaEvent_t done = nullptr;
-  cudaEvent_t prof[5] = {nullptr, nullptr, nullptr, nullptr, nullptr};
+  static constexpr int kStages = 8;
+  cudaEvent_t prof[kStages + 1] = {};
   bool profiling = false;
   bool profiled_run = false;
   bool pending = false;  // an async parse is in flight
@@ -95,8 +111,9 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
   if (p->done) cudaEventDestroy(p->done);
   for (cudaEvent_t e : p->prof)
     if (e) cudaEventDestroy(e);
-  void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_s1_state,
-                 p->d_s1_count, p->d_tile_cnt, p->d_tile_off, p->d_s2, p->d_s2_flag, p->d_surv,
+  void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_tile_cnt,
+                 p->d_tile_off, p->d_s1_rec, p->d_s1_pre, p->d_s1_blk, p->d_s2_rec, p->d_s2_pre,
+                 p->d_scan_agg, p->d_scan_pre, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
                  p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job};
   for (void *q : dev)
@@ -119,12 +136,21 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(&p->d_doc_off, (uint64_t)max_docs + 1))) return r;
   if ((r = dalloc(&p->d_tile_first, (uint64_t)max_docs + 1))) return r;
   if ((r = dalloc(&p->d_counters, 4))) return r;
-  if ((r = dalloc(&p->d_s1_state, tiles))) return r;
-  if ((r = dalloc(&p->d_s1_count, tiles))) return r;
+  p->scan_blocks = (uint32_t)((tiles + sj::kScanBlock - 1) / sj::kScanBlock);
+  p->spt_levels = 2;
+  while ((1ull << (p->spt_levels - 1)) <= tiles) p->spt_levels++;
   if ((r = dalloc(&p->d_tile_cnt, tiles))) return r;
   if ((r = dalloc(&p->d_tile_off, tiles))) return r;
-  if ((r = dalloc(&p->d_s2, tiles))) return r;
-  if ((r = dalloc(&p->d_s2_flag, tiles))) return r;
+  if ((r = dalloc(&p->d_s1_rec, tiles))) return r;
+  if ((r = dalloc(&p->d_s1_pre, tiles))) return r;
+  if ((r = dalloc(&p->d_s1_blk, tiles * 64))) return r;
+  if ((r = dalloc(&p->d_s2_rec, tiles))) return r;
+  if ((r = dalloc(&p->d_s2_pre, tiles))) return r;
+  if ((r = dalloc(&p->d_scan_agg, p->scan_blocks))) return r;
+  if ((r = dalloc(&p->d_scan_pre, p->scan_blocks))) return r;
+  if ((r = dalloc(&p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
+  if ((r = dalloc(&p->d_slen, max_bytes + 16))) return r;
+  if ((r = dalloc(&p->d_front, max_bytes + tiles + 16))) return r;
   if ((r = dalloc(&p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_idx, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
@@ -137,9 +163,6 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(&p->d_results, max_docs))) return r;
   if ((r = dalloc(&p->d_job, 1))) return r;
   CK(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t)));
-  CK(cudaMemset(p->d_s1_state, 0, tiles * sizeof(uint32_t)));
-  CK(cudaMemset(p->d_s1_count, 0, tiles * sizeof(uint64_t)));
-  CK(cudaMemset(p->d_s2_flag, 0, tiles * sizeof(uint32_t)));
   CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
   CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
   CK(cudaMallocHost((void **)&p->h_results, (size_t)max_docs * sizeof(sj_doc_result)));
@@ -149,11 +172,13 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
 
   int sms = 0, occ1 = 0, occ2 = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_kernel, 32 * sj::kS1Warps, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sj::stage2_kernel, sj::kS2Threads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_blocks_kernel,
+                                                   32 * sj::kS1Warps, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sj::stage2_build_kernel, sj::kS2Threads, 0));
   p->s1_grid = sms * (occ1 > 0 ? occ1 : 1);
   p->s2_grid = sms * (occ2 > 0 ? occ2 : 1);
   p->fin_grid = sms * 4;
+  p->aux_grid = sms * 8;
 
   Job &J = *p->h_job;
   memset(&J, 0, sizeof(J));
@@ -162,12 +187,20 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.max_doc_len = sj::kMaxDocBytes;
   J.tile_first = p->d_tile_first;
   J.counters = p->d_counters;
-  J.s1_state = p->d_s1_state;
-  J.s1_count = p->d_s1_count;
   J.tile_cnt = p->d_tile_cnt;
   J.tile_off = p->d_tile_off;
-  J.s2 = p->d_s2;
-  J.s2_flag = p->d_s2_flag;
+  J.s1_rec = p->d_s1_rec;
+  J.s1_pre = p->d_s1_pre;
+  J.s1_blk = p->d_s1_blk;
+  J.s2_rec = p->d_s2_rec;
+  J.s2_pre = p->d_s2_pre;
+  J.scan_agg = p->d_scan_agg;
+  J.scan_pre = p->d_scan_pre;
+  J.spt = p->d_spt;
+  J.spt_stride = (uint32_t)tiles;
+  J.spt_levels = p->spt_levels;
+  J.slen = p->d_slen;
+  J.front = p->d_front;
   J.surv = p->d_surv;
   J.idx = p->d_idx;
   J.tape = p->d_tape;
@@ -199,6 +232,37 @@ extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint3
   return SJ_SUCCESS;
 }
 
+// The kernels of one run, in order.  With `ev`, an event is recorded before
+// the first kernel and after each of the stages named in STAGE_NAMES.
+static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+  if (ev) cudaEventRecord(ev[0], s);
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[1], s);
+  sj::stage1_blocks_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[2], s);
+  sj::launch_scan1(p->d_job, p->scan_blocks, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  sj::stage1_flatten_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[4], s);
+  sj::stage2_reduce_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[5], s);
+  sj::launch_scan2(p->d_job, p->scan_blocks, s);
+  for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
+    sj::spt_build_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job, src);
+  sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
+  sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[6], s);
+  sj::stage2_build_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[7], s);
+  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[8], s);
+}
+
+static uint32_t kernels_per_run(const sj_parser *p) {
+  return 2 /* setup, blocks */ + 3 + 1 /* scan1, flatten */ + 1 + 3 /* reduce, scan2 */ +
+         (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 + 1 /* build, finalize */;
+}
+
 // Capture (once per document count) the launch sequence of one run.
 static int ensure_graph(sj_parser *p, uint32_t n_docs) {
   if (p->graph && p->graph_docs == n_docs) return SJ_SUCCESS;
@@ -212,10 +276,7 @@ static int ensure_graph(sj_parser *p, uint32_t n_docs) {
   cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s);
   cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
                   cudaMemcpyHostToDevice, s);
-  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
-  sj::stage1_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
-  sj::stage2_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
-  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  enqueue_run(p, s, nullptr);
   cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
                   cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamEndCapture(s, &g);
@@ -263,15 +324,7 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
     CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
                        cudaMemcpyHostToDevice, stream));
-    CK(cudaEventRecord(p->prof[0], stream));
-    sj::setup_kernel<<<1, 1024, 0, stream>>>(p->d_job);
-    CK(cudaEventRecord(p->prof[1], stream));
-    sj::stage1_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, stream>>>(p->d_job);
-    CK(cudaEventRecord(p->prof[2], stream));
-    sj::stage2_kernel<<<p->s2_grid, sj::kS2Threads, 0, stream>>>(p->d_job);
-    CK(cudaEventRecord(p->prof[3], stream));
-    sj::finalize_kernel<<<p->fin_grid, 256, 0, stream>>>(p->d_job);
-    CK(cudaEventRecord(p->prof[4], stream));
+    enqueue_run(p, stream, p->prof);
     CK(cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
                        cudaMemcpyDeviceToHost, stream));
     CK(cudaGetLastError());
@@ -367,12 +420,17 @@ extern "C" sj_status sj_parser_set_profiling(sj_parser *p, int enable) {
   return SJ_SUCCESS;
 }
 
-extern "C" sj_status sj_parser_stage_times(sj_parser *p, float ms[4]) {
-  if (!p || !ms) return SJ_INVALID_ARG;
+extern "C" sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n) {
+  if (!p || !ms || n < sj_parser::kStages) return SJ_INVALID_ARG;
   if (!p->profiled_run) return SJ_INVALID_ARG;
-  CK(cudaEventSynchronize(p->prof[4]));
-  for (int i = 0; i < 4; i++) CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+  CK(cudaEventSynchronize(p->prof[sj_parser::kStages]));
+  for (int i = 0; i < sj_parser::kStages; i++)
+    CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
   return SJ_SUCCESS;
+}
+
+extern "C" int sj_parser_kernels_per_run(const sj_parser *p) {
+  return p ? (int)kernels_per_run(p) : 0;
 }
 
 extern "C" const char *sj_error_name(int code) {

@@ -1,0 +1,171 @@
+// s1.cu -- stage 1 of the parser (Sec. 3.1), reduce-then-scan form.
+//
+// One warp takes a tile of 2 KiB: each lane owns one 64-byte block, the
+// paper's unit of work, and builds its 64-bit masks with SWAR classification.
+// The paper carries three facts from one block to the next (footnote of Sec.
+// 3.1.1): whether an odd backslash run is pending, whether the scan is inside a
+// string, and whether the previous byte separates tokens.  Between the lanes of
+// a tile they travel by warp votes and shuffles.  Between tiles, two of them
+// are read directly from the bytes before the tile (the backslash run, and the
+// class of the previous byte); only the in-string bit needs the whole prefix
+// of the document.  So stage1_blocks_kernel computes, for both values of the
+// incoming in-string bit, the final structural mask of every block and the
+// tile's index count; a segmented scan over tiles (scan.cu) then fixes the bit
+// and the output offset of every tile, and stage1_flatten_kernel writes the
+// indices.  No kernel waits on another block.
+#include "s1_common.cuh"
+
+namespace sj {
+
+// Length of the backslash run that ends just before document position `end`
+// (lanes test 32 bytes at a time going backwards).
+__device__ __forceinline__ uint64_t bs_run_before(const uint8_t *doc, uint64_t end, int lane) {
+  uint64_t run = 0, pos = end;
+  for (;;) {
+    const bool bs = pos > (uint64_t)lane && doc[pos - 1 - lane] == '\\';
+    const unsigned m = __ballot_sync(0xFFFFFFFFu, bs);
+    if (m != 0xFFFFFFFFu) return run + (uint64_t)(__ffs(~m) - 1);
+    run += 32;
+    pos -= 32;
+  }
+}
+
+// How the byte before a tile makes its first byte a token start.
+enum : uint32_t { kSepNever = 0, kSepAlways = 1, kSepIfOutside = 2 };
+
+__global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job *__restrict__ job) {
+  const Job &J = *job;
+  const int lane = threadIdx.x & 31;
+  const uint32_t n_tiles = J.counters[2];
+  const uint32_t warps = gridDim.x * kS1Warps;
+  for (uint32_t t = blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const uint32_t d = doc_of_tile(J, t);
+    const uint32_t tt = t - J.tile_first[d];
+    const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
+    const uint8_t *doc = J.base + J.doc_off[d];
+    const uint64_t t0 = (uint64_t)tt * kTileBytes;
+    const uint64_t blk = t0 + (uint64_t)lane * kBlockBytes;
+
+    uint32_t w[16];
+    load_block(doc, len, blk, w);
+    BlockMasks m;
+    classify_block(w, m);
+
+    // ---- UTF-8 (Sec. 3.1.5) --------------------------------------------------
+    {
+      uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, w[15], 1);
+      int nprev = 3;
+      if (lane == 0) {
+        prev = 0;
+        nprev = blk >= 3 ? 3 : (int)blk;
+        for (int k = 0; k < nprev; k++) prev |= (uint32_t)doc[blk - nprev + k] << (8 * (4 - nprev + k));
+      }
+      const bool need = m.nonascii != 0 || (prev & (prev << 1) & 0x80808000u);
+      const bool ends_here = blk < len && blk + 64 >= len;
+      if (blk < len && need && utf8_block_error(w, prev, nprev, ends_here))
+        atomicOr(&J.doc_flags[d], kFlagUtf8);
+    }
+
+    // ---- carries read from the bytes before the tile --------------------------
+    uint32_t e_in = 0, sep_rule = kSepAlways;  // byte -1 of a document: virtual white space
+    if (tt > 0) {
+      e_in = (uint32_t)(bs_run_before(doc, t0, lane) & 1);
+      const uint8_t c = doc[t0 - 1];
+      if (c == ' ' || c == '\n' || c == '\r' || c == '\t') sep_rule = kSepAlways;
+      else if (c == ',' || c == ':' || c == '[' || c == ']' || c == '{' || c == '}') sep_rule = kSepIfOutside;
+      else if (c == '"') sep_rule = (bs_run_before(doc, t0 - 1, lane) & 1) ? kSepNever : kSepAlways;
+      else sep_rule = kSepNever;
+    }
+
+    // ---- escapes (Fig. "identifyescapedquotes") and real quotes ---------------
+    const bool all_bs = (m.bs == ~0ull);
+    const uint32_t tail = (uint32_t)__clzll((long long)~m.bs) & 1u;  // trailing run parity
+    const unsigned nb = __ballot_sync(0xFFFFFFFFu, !all_bs);
+    const unsigned tb = __ballot_sync(0xFFFFFFFFu, tail);
+    const unsigned below = (1u << lane) - 1u;
+    uint32_t e_lane = e_in;
+    if (nb & below) e_lane = (tb >> (31 - __clz(nb & below))) & 1u;
+    const uint64_t od = escaped_no_carry(m.bs) ^ (e_lane ? first_non_bs(m.bs) : 0ull);
+    const uint64_t Q = m.quote & ~od;
+    const unsigned pb = __ballot_sync(0xFFFFFFFFu, __popcll(Q) & 1u);
+    const uint32_t q_before = __popc(pb & below) & 1u;  // real quotes in earlier lanes, mod 2
+    const uint64_t RQ = prefix_xor(Q);
+
+    // ---- final masks (Figs. "identifyquoteregion", "identifypseudo") for both
+    //      values h of the in-string bit entering the tile -----------------------
+    uint64_t S[2];
+    uint32_t cnt[2];
+#pragma unroll
+    for (int h = 0; h < 2; h++) {
+      const uint64_t R = RQ ^ (((uint32_t)h ^ q_before) ? ~0ull : 0ull);
+      const uint64_t S1 = (m.op & ~R) | Q;
+      const uint64_t SW = S1 | m.ws;
+      uint32_t sep_in = __shfl_up_sync(0xFFFFFFFFu, (uint32_t)(SW >> 63), 1);
+      if (lane == 0) sep_in = sep_rule == kSepAlways ? 1u : (sep_rule == kSepIfOutside ? (uint32_t)(h ^ 1) : 0u);
+      const uint64_t P = ((SW << 1) | sep_in) & ~m.ws & ~R;
+      S[h] = (S1 | P) & ~(Q & ~R);
+      uint32_t c = __popcll(S[h]);
+#pragma unroll
+      for (int o = 16; o; o >>= 1) c += __shfl_xor_sync(0xFFFFFFFFu, c, o);
+      cnt[h] = c;
+    }
+    reinterpret_cast<ulonglong2 *>(J.s1_blk)[(uint64_t)t * 32 + lane] = make_ulonglong2(S[0], S[1]);
+    if (lane == 0) {
+      S1Agg a;
+      a.qpar = __popc(pb) & 1u;
+      a.c0 = cnt[0];
+      a.c1 = cnt[1];
+      a.head = tt == 0;
+      J.s1_rec[t] = a;
+    }
+  }
+}
+
+// After the tile scan: pick each block's mask for the actual in-string bit,
+// and write the indices (Sec. 3.1.4) at the tile's offset, staged in shared
+// memory so that the stores are coalesced.
+__global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job *__restrict__ job) {
+  const Job &J = *job;
+  __shared__ uint32_t stage[kS1Warps][kTileBytes];
+  const int lane = threadIdx.x & 31;
+  uint32_t *out_stage = stage[threadIdx.x >> 5];
+  const uint32_t n_tiles = J.counters[2];
+  const uint32_t warps = gridDim.x * kS1Warps;
+  for (uint32_t t = blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const uint32_t d = doc_of_tile(J, t);
+    const uint32_t tt = t - J.tile_first[d];
+    const uint32_t ntiles_d = J.tile_first[d + 1] - J.tile_first[d];
+    const S1Pre pre = J.s1_pre[t];
+    const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(J.s1_blk)[(uint64_t)t * 32 + lane];
+    const uint64_t S = pre.q_in ? v.y : v.x;
+    const uint32_t c = __popcll(S);
+    uint32_t incl = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
+      if (lane >= o) incl += u;
+    }
+    const uint32_t n = __shfl_sync(0xFFFFFFFFu, incl, 31);
+    uint32_t o = incl - c;
+    uint64_t s = S;
+    const uint32_t pos0 = tt * kTileBytes + lane * kBlockBytes;
+    while (s) {
+      out_stage[o++] = pos0 + (uint32_t)(__ffsll((long long)s) - 1);
+      s &= s - 1;
+    }
+    __syncwarp();
+    uint32_t *dst = J.idx + idx_base(J, d) + pre.base;
+    for (uint32_t k = lane; k < n; k += 32) dst[k] = out_stage[k];
+    __syncwarp();
+    if (lane == 0) {
+      J.tile_cnt[t] = n;
+      J.tile_off[t] = pre.base;
+      if (tt == ntiles_d - 1) {
+        J.doc_nidx[d] = pre.base + n;
+        if (pre.q_in ^ J.s1_rec[t].qpar) atomicOr(&J.doc_flags[d], kFlagUnclosed);
+      }
+    }
+  }
+}
+
+}  // namespace sj

@@ -8,7 +8,7 @@ namespace sj {
 
 // Stage 1 (Sec. 3.1) works on 64-byte blocks as in the paper: one block per
 // lane, one warp per tile of 32 blocks.  Stage 2 (Sec. 3.2) processes the
-// indices of one stage-1 tile per thread block.
+// indices of one stage-1 tile per thread block.  Tiles never span documents.
 constexpr int kBlockBytes = 64;
 constexpr int kTileBytes = 32 * kBlockBytes;  // 2048
 constexpr int kS1Warps = 4;                   // tiles (warps) per stage-1 thread block
@@ -24,23 +24,33 @@ constexpr uint32_t kFlagUtf8 = 1, kFlagUnclosed = 2, kFlagInternal = 4, kFlagCap
 // Look-back status values (top two bits of a status word).
 constexpr uint32_t kStAgg = 1, kStIncl = 2;
 
-// Per-tile record of the stage-2 look-back (Sec. 3.2 state carried between
-// tiles: nesting depth, tape slots, string-buffer bytes).
-struct S2Tile {
-  // aggregate of the tile alone (published with kStAgg)
-  int32_t d_delta;     // depth change over the tile
-  int32_t min_rel;     // lowest depth reached, relative to the tile start (<= 0)
-  uint32_t words;      // tape words written by the tile's tokens
-  uint32_t pad0;
-  uint64_t strbytes;   // string-buffer bytes of the tile's strings
-  // inclusive prefix (published with kStIncl)
-  int32_t d_start;     // absolute depth before the tile's first token
-  uint32_t jump;       // nearest earlier tile of the document with a lower `low`, or kNoTile
-  uint32_t tape_start; // tape index of the tile's first word (document relative)
-  uint32_t pad1;
-  uint64_t str_start;  // string-buffer offset of the tile's first string (document relative)
-};
 constexpr uint32_t kNoTile = 0xFFFFFFFFu;
+
+// Stage-1 tile aggregate (Sec. 3.1, carried in-string bit): the parity of the
+// tile's real quotes and its index counts when it is entered outside (c0) or
+// inside (c1) a string.  `head` marks the first tile of a document.
+struct S1Agg {
+  uint32_t qpar, c0, c1, head;
+};
+// Stage-1 tile prefix: the in-string bit entering the tile and its index offset.
+struct S1Pre {
+  uint32_t base, q_in;
+};
+// Stage-2 tile aggregate: depth change, lowest depth reached relative to the
+// tile start (<= 0), tape words and string-buffer bytes of its tokens.
+struct S2Agg {
+  int32_t dd, mn;
+  uint32_t w, head;
+  uint64_t s;
+};
+// Stage-2 tile prefix: absolute depth before the tile, its lowest depth, its
+// first tape index and string-buffer offset (document relative).
+struct S2Pre {
+  int32_t d_start, low;
+  uint32_t tape_start, jump;  // jump: nearest earlier tile of the document with a lower `low`
+  uint64_t str_start;
+};
+constexpr int kScanBlock = 1024;  // tiles per thread block in the tile scans
 
 // Everything a run needs, in device memory (one copy per parser; refreshed
 // by a host-to-device copy before each run so that one captured graph serves
@@ -53,14 +63,24 @@ struct Job {
   uint64_t max_doc_len;
   // scratch
   uint32_t *tile_first;     // n_docs + 1: first stage-1 tile of each document
-  uint32_t *counters;       // [0] stage-1 ticket, [1] stage-2 ticket, [2] number of tiles
+  uint32_t *counters;       // [0] look-back ticket, [2] number of tiles
   uint32_t *s1_state;       // per tile: escape/quote/separator look-back word
   uint64_t *s1_count;       // per tile: index-count look-back word
   uint32_t *tile_cnt;       // per tile: indices produced
   uint32_t *tile_off;       // per tile: document-relative offset of its first index
-  S2Tile *s2;               // per tile
-  uint32_t *s2_flag;        // per tile
   uint32_t *surv;           // per index slot: open containers left by a tile (by level)
+  // reduce-then-scan state
+  S1Agg *s1_rec;            // per tile
+  S1Pre *s1_pre;            // per tile
+  uint64_t *s1_blk;         // per 64-byte block: final mask entered outside / inside a string
+  S2Agg *s2_rec;            // per tile
+  S2Pre *s2_pre;            // per tile
+  void *scan_agg;           // per scan block (sized for S2Agg)
+  void *scan_pre;           // per scan block
+  int32_t *spt;             // sparse table of tile `low` minima: level k at spt + k * spt_stride
+  uint32_t spt_stride, spt_levels;
+  uint32_t *slen;           // per index slot: normalised length of the string token there
+  uint64_t *front;          // per index slot + tile: open container of each level entering a tile
   // outputs
   uint32_t *idx;
   uint64_t *tape;
