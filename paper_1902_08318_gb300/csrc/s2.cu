@@ -28,138 +28,191 @@ __device__ __forceinline__ void report(const Job &J, uint32_t d, uint64_t token,
   atomicMin(&J.doc_err[d], (unsigned long long)((token << 8) | (uint64_t)code));
 }
 
-// Exclusive scan over the threads of the block of (depth sum, tape words) and
-// the running minimum of the depth, in token order (each thread owns a
-// contiguous run of tokens).  Returns the block totals through the pointers.
-struct DW {
-  int32_t d, mn;
-  uint32_t w, n;  // n: a count (strings) scanned alongside
+// ---- one warp per tile ---------------------------------------------------
+constexpr int kS2Warps = kS2Threads / 32;
+constexpr int kHalo = 1024;                    // staged bytes past the tile's end
+constexpr int kStageBytes = kTileBytes + kHalo;
+constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
+
+// Per-warp shared state.  `open[l]` is the container currently open at
+// relative level l (levels are depths after an opener, relative to the tile
+// start), written by openers of this tile: 0 = none, else bit 15 set,
+// bit 14 = object, bits 0-11 = the opener's tape slot relative to the tile.
+struct __align__(16) WarpSmem {  // 16-byte aligned size: bytes[] of every warp takes uint4 stores
+  uint8_t bytes[kStageBytes + 64];
+  uint16_t open[2 * kMaxTileTokens + 1];
 };
-__device__ __forceinline__ DW dw_combine(const DW &a, const DW &b) {
-  return DW{a.d + b.d, min(a.mn, a.d + b.mn), a.w + b.w, a.n + b.n};
-}
-__device__ DW block_exclusive_dw(DW v, DW *s_warp, DW &total) {
-  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  DW x = v;
+static_assert(sizeof(WarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+
+__device__ __forceinline__ uint32_t warp_incl_u32(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
-    DW u;
-    u.d = __shfl_up_sync(0xFFFFFFFFu, x.d, o);
-    u.mn = __shfl_up_sync(0xFFFFFFFFu, x.mn, o);
-    u.w = __shfl_up_sync(0xFFFFFFFFu, x.w, o);
-    u.n = __shfl_up_sync(0xFFFFFFFFu, x.n, o);
-    if (lane >= o) x = dw_combine(u, x);
+    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += u;
   }
-  if (lane == 31) s_warp[wid] = x;
-  __syncthreads();
-  DW pre{0, 0, 0, 0};
-  for (int i = 0; i < wid; i++) pre = dw_combine(pre, s_warp[i]);
-  total = DW{0, 0, 0, 0};
-  for (int i = 0; i < kS2Threads / 32; i++) total = dw_combine(total, s_warp[i]);
-  DW xe;  // exclusive within the warp
-  xe.d = __shfl_up_sync(0xFFFFFFFFu, x.d, 1);
-  xe.mn = __shfl_up_sync(0xFFFFFFFFu, x.mn, 1);
-  xe.w = __shfl_up_sync(0xFFFFFFFFu, x.w, 1);
-  xe.n = __shfl_up_sync(0xFFFFFFFFu, x.n, 1);
-  if (lane == 0) xe = DW{0, 0, 0, 0};
-  __syncthreads();
-  return dw_combine(pre, xe);
+  return v;
+}
+__device__ __forceinline__ int32_t warp_incl_i32(int32_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
 }
 
-// Shared per-tile state of both stage-2 kernels.
-struct TileSmem {
-  uint32_t pos[kMaxTileTokens + 1];  // token positions (+ the next token's)
-  int16_t D[kMaxTileTokens];         // depth after the token, relative to the tile start
-  uint16_t tape[kMaxTileTokens];     // tape slot relative to the tile
-  uint8_t kind[kMaxTileTokens];
-  uint16_t list[kMaxTileTokens];     // strings, then numbers (token indices)
-  uint32_t closed[kMaxTileTokens / 32];
-  int16_t chunkmin[kMaxTileTokens / 32];
-  DW warp[kS2Threads / 32];
-  uint32_t n_str, n_num;
-  unsigned long long strbytes;
+// Staged view of the document around one tile.
+struct Staged {
+  const uint8_t *doc;   // global
+  uint64_t len;
+  int64_t sbase;        // document position of bytes[0]
+  uint64_t slimit;      // first document position not staged
+  const uint8_t *smem;
+  __device__ __forceinline__ uint8_t at(uint64_t p) const {
+    return (p < slimit && (int64_t)p >= sbase) ? smem[p - sbase] : doc[p];
+  }
+  // pointer for reading [p, q): shared memory when staged, else global
+  __device__ __forceinline__ const uint8_t *ptr(uint64_t p, uint64_t q) const {
+    return (q <= slimit && (int64_t)p >= sbase) ? smem + (p - sbase) : doc + p;
+  }
 };
 
-// Loads the tile's token positions and kinds and lists its strings (in token
-// order) and numbers.  Then the blocked depth / tape-word scan.
-__device__ void tile_tokens(const Job &J, TileSmem &S, const uint32_t *idxp, const uint8_t *doc,
-                            uint64_t len, uint32_t off, uint32_t cnt, uint32_t nidx, DW &tot,
-                            uint32_t &a, uint32_t &b, DW &ex) {
-  const int tid = threadIdx.x;
-  for (uint32_t j = tid; j < cnt; j += kS2Threads) {
-    const uint32_t p = idxp[off + j];
-    S.pos[j] = p;
-    S.kind[j] = token_kind(doc[p]);
-  }
-  if (tid == 0) {
-    S.pos[cnt] = (off + cnt < nidx) ? idxp[off + cnt] : (uint32_t)len;
-    S.n_num = 0;
-    S.strbytes = 0;
-  }
-  for (uint32_t j = tid; j < kMaxTileTokens / 32; j += kS2Threads) S.closed[j] = 0;
-  __syncthreads();
-  const uint32_t per = (cnt + kS2Threads - 1) / kS2Threads;
-  a = min(cnt, tid * per);
-  b = min(cnt, a + per);
-  DW v{0, 0, 0, 0};
-  for (uint32_t j = a; j < b; j++) {
-    const uint8_t k = S.kind[j];
-    v.d += depth_delta(k);
-    v.mn = min(v.mn, v.d);
-    v.w += tape_words_of(k);
-    v.n += k == K_STRING;
-  }
-  ex = block_exclusive_dw(v, S.warp, tot);
-  {
-    int32_t r = ex.d;
-    uint32_t wr = ex.w, sn = ex.n;
-    for (uint32_t j = a; j < b; j++) {
-      const uint8_t k = S.kind[j];
-      r += depth_delta(k);
-      S.D[j] = (int16_t)r;
-      S.tape[j] = (uint16_t)wr;
-      wr += tape_words_of(k);
-      if (k == K_STRING) S.list[sn++] = (uint16_t)j;
-    }
-  }
-  if (tid == 0) S.n_str = tot.n;
-  __syncthreads();
-  for (uint32_t c = tid; c * 32 < cnt; c += kS2Threads) {
-    int32_t mn = 0x7FFF;
-    const uint32_t e = min(cnt, c * 32 + 32);
-    for (uint32_t j = c * 32; j < e; j++) mn = min(mn, (int32_t)S.D[j]);
-    S.chunkmin[c] = (int16_t)mn;
-  }
-  __syncthreads();
+__device__ __forceinline__ Staged stage_tile(WarpSmem &W, const uint8_t *doc, uint64_t len,
+                                             uint64_t t0, int lane) {
+  const uintptr_t g0 = (uintptr_t)(doc + t0);
+  const uintptr_t a0 = g0 & ~(uintptr_t)15;
+  const uintptr_t dend = (uintptr_t)doc + len;
+  const uintptr_t send = min((uintptr_t)(a0 + kStageBytes), dend);
+  const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
+  for (uint32_t c = lane; c < nch; c += 32)
+    reinterpret_cast<uint4 *>(W.bytes)[c] = __ldg(reinterpret_cast<const uint4 *>(a0 + 16 * c));
+  __syncwarp();
+  Staged v;
+  v.doc = doc;
+  v.len = len;
+  v.sbase = (int64_t)t0 - (int64_t)(g0 - a0);
+  v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
+  v.smem = W.bytes;
+  return v;
 }
 
-// Parent of token j inside the tile: the token after the last one whose depth
-// is at most (depth before j) - 1, or -1 if that lies before the tile.
-__device__ __forceinline__ int32_t tile_parent(const TileSmem &S, uint32_t j, int32_t pmin_before) {
-  const int32_t E = j ? S.D[j - 1] : 0;
-  const int32_t x = E - 1;
-  if (x < pmin_before) return -1;
-  int32_t m = (int32_t)j - 1;
-  while (m >= 0) {
-    if ((m & 31) == 31 && S.chunkmin[m >> 5] > x) { m -= 32; continue; }
-    if (S.D[m] <= x) break;
-    m--;
+// Tokens of one tile, 32 at a time: positions, kinds, depths, tape slots and
+// the enclosing container of each token (from the warp's level table, or -1
+// when it was opened before the tile).
+struct Chunk {
+  uint32_t j;       // token index in the tile
+  bool valid;
+  uint32_t pos, next;
+  uint8_t kind;
+  int32_t E, D;     // relative depth before / after the token
+  uint32_t tape;    // relative tape slot
+  uint32_t sord;    // string ordinal in the tile (strings before this token)
+  uint16_t parent;  // open[] entry of the enclosing container, 0 = before the tile
+};
+
+struct TileWalk {
+  int32_t depth = 0, dmin = 0, dmax = 0;
+  uint32_t tape = 0, nstr = 0;
+  uint32_t pos_next = 0;  // first position of the next chunk
+
+  __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt,
+                                        uint32_t nidx, uint64_t len, int lane) {
+    const uint32_t j = lane;
+    pos_next = j < cnt ? idxp[off + j] : 0u;
+    (void)nidx;
+    (void)len;
   }
-  return m + 1;
-}
+
+  __device__ __forceinline__ void next(Chunk &c, WarpSmem &W, const Staged &sv, const uint32_t *idxp,
+                                       uint32_t off, uint32_t cnt, uint32_t nidx, uint64_t len,
+                                       uint32_t base, int lane) {
+    c.j = base + lane;
+    c.valid = c.j < cnt;
+    c.pos = pos_next;
+    // prefetch the next chunk
+    const uint32_t jn = base + 32 + lane;
+    pos_next = jn < cnt ? idxp[off + jn] : 0u;
+    uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, c.pos, 1);
+    const uint32_t first_next = __shfl_sync(0xFFFFFFFFu, pos_next, 0);
+    if (lane == 31 || c.j + 1 == cnt) {
+      const uint32_t g = off + c.j + 1;  // document index of the next token
+      nx = (c.j + 1 < cnt) ? first_next : (g < nidx ? idxp[g] : (uint32_t)len);
+    }
+    c.next = nx;
+    c.kind = c.valid ? token_kind(sv.at(c.pos)) : K_OTHER;
+    const int32_t dl = c.valid ? depth_delta(c.kind) : 0;
+    const int32_t di = warp_incl_i32(dl, lane);
+    c.D = depth + di;
+    c.E = c.D - dl;
+    const uint32_t w = c.valid ? tape_words_of(c.kind) : 0u;
+    const uint32_t wi = warp_incl_u32(w, lane);
+    c.tape = tape + wi - w;
+    const uint32_t si = __ballot_sync(0xFFFFFFFFu, c.valid && c.kind == K_STRING);
+    c.sord = nstr + __popc(si & ((1u << lane) - 1u));
+    // parents: the last opener of this chunk at the token's level, else the table
+    const bool op = c.valid && is_open(c.kind);
+    uint16_t my = op ? (uint16_t)(0x8000u | (c.kind == K_OPEN_OBJ ? 0x4000u : 0u) | c.tape) : 0;
+    c.parent = 0;
+    unsigned pending = __ballot_sync(0xFFFFFFFFu, c.valid);
+    const unsigned below = (1u << lane) - 1u;
+    while (pending) {
+      const int32_t lv = __shfl_sync(0xFFFFFFFFu, c.E, __ffs(pending) - 1);
+      const unsigned opl = __ballot_sync(0xFFFFFFFFu, op && c.D == lv);
+      const bool mine = ((pending >> lane) & 1u) && c.E == lv;
+      const unsigned m = opl & below;
+      const int src = (mine && m) ? 31 - __clz(m) : lane;
+      const uint16_t got = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, src);
+      if (mine) {
+        if (m) c.parent = got;
+        else if (lv > -kLevelOff && lv <= kLevelOff) c.parent = W.open[lv + kLevelOff];
+      }
+      pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
+    }
+    // the last opener of each level of this chunk stays open for later tokens
+    const unsigned grp = __match_any_sync(0xFFFFFFFFu, op ? c.D : 0x7FFFFFFF);
+    if (op && lane == 31 - __clz(grp)) W.open[c.D + kLevelOff] = my;
+    // advance
+    depth += __shfl_sync(0xFFFFFFFFu, di, 31);
+    tape += __shfl_sync(0xFFFFFFFFu, wi, 31);
+    nstr += __popc(si);
+    int32_t mn = c.valid ? min(c.E, c.D) : 0x7FFFFFFF, mx = c.valid ? max(c.E, c.D) : -0x7FFFFFFF;
+#pragma unroll
+    for (int o = 16; o; o >>= 1) {
+      mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    dmin = min(dmin, mn);
+    dmax = max(dmax, mx);
+    __syncwarp();
+  }
+
+  // forget this tile's levels
+  __device__ __forceinline__ void clear(WarpSmem &W, int lane) {
+    for (int32_t v = max(dmin, -kLevelOff) + lane; v <= min(dmax, kLevelOff); v += 32)
+      W.open[v + kLevelOff] = 0;
+    __syncwarp();
+  }
+};
 
 // ---------------------------------------------------------------------------
+// Stage-2 reduce: per tile, the depth change and lowest depth, tape words,
+// string-buffer bytes (string lengths are stored for the build pass), and the
+// containers left open at each level (the survivors).
 __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ TileSmem S;
-  const int tid = threadIdx.x;
+  __shared__ WarpSmem WS[kS2Warps];
+  const int lane = threadIdx.x & 31;
+  WarpSmem &W = WS[threadIdx.x >> 5];
+  for (uint32_t i = lane; i < 2 * kMaxTileTokens + 1; i += 32) W.open[i] = 0;
+  __syncwarp();
   const uint32_t n_tiles = J.counters[2];
-  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  const uint32_t warps = gridDim.x * kS2Warps;
+  for (uint32_t t = blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint32_t nidx = J.doc_nidx[d];
     if ((J.doc_flags[d] & kDocBad) || nidx == 0) {
-      if (tid == 0) J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
+      if (lane == 0) J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
       continue;
     }
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
@@ -167,55 +220,49 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const uint64_t ib = idx_base(J, d);
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
-    DW tot, ex;
-    uint32_t a, b;
-    tile_tokens(J, S, idxp, doc, len, off, cnt, nidx, tot, a, b, ex);
-
-    // normalised string lengths (Sec. 3.2.2), one string per thread at a time
-    unsigned long long sb = 0;
-    for (uint32_t i = tid; i < S.n_str; i += kS2Threads) {
-      const uint32_t j = S.list[i];
-      int err;
-      const uint32_t n = string_walk<false>(doc + S.pos[j] + 1, doc + S.pos[j + 1], err, nullptr);
-      J.slen[ib + off + j] = err ? (0x80000000u | (uint32_t)err) : n;
-      sb += 5ull + (err ? 0 : n);
-    }
-    if (sb) atomicAdd(&S.strbytes, sb);
-
-    // containers closed inside the tile; the others are left open (survivors)
-    {
-      int32_t pmin = min(0, ex.mn);
-      for (uint32_t j = a; j < b; j++) {
-        if (is_close(S.kind[j])) {
-          const int32_t par = tile_parent(S, j, pmin);
-          if (par >= 0) atomicOr(&S.closed[par >> 5], 1u << (par & 31));
-        }
-        pmin = min(pmin, (int32_t)S.D[j]);
+    const Staged sv = stage_tile(W, doc, len, (uint64_t)tt * kTileBytes, lane);
+    TileWalk tw;
+    tw.begin(idxp, off, cnt, nidx, len, lane);
+    uint64_t sb = 0;
+    for (uint32_t base = 0; base < cnt; base += 32) {
+      Chunk c;
+      tw.next(c, W, sv, idxp, off, cnt, nidx, len, base, lane);
+      if (c.valid && c.kind == K_STRING) {  // normalised length (Sec. 3.2.2)
+        int err;
+        const uint64_t p0 = (uint64_t)c.pos + 1, p1 = c.next;
+        const uint8_t *sp = sv.ptr(p0, p1);
+        const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
+        J.slen[ib + off + c.j] = err ? (0x80000000u | (uint32_t)err) : n;
+        sb += 5ull + (err ? 0 : n);
       }
     }
-    __syncthreads();
-    const int32_t min_rel = min(0, tot.mn);
-    for (uint32_t j = tid; j < cnt; j += kS2Threads) {
-      const uint8_t k = S.kind[j];
-      if (is_open(k) && !((S.closed[j >> 5] >> (j & 31)) & 1u)) {
-        const int32_t slot = S.D[j] - min_rel - 1;
-        J.surv[ib + off + slot] = (k == K_OPEN_OBJ ? 0x80000000u : 0u) | S.tape[j];
-      }
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+    // survivors: the open container of each level in (dmin, depth]
+    const int32_t lo = tw.dmin;
+    for (int32_t lv = lo + 1 + lane; lv <= tw.depth; lv += 32) {
+      const uint16_t e = W.open[lv + kLevelOff];
+      J.surv[ib + off + (uint32_t)(lv - lo - 1)] = ((uint32_t)(e >> 14) & 1u) << 31 | (e & 0x0FFFu);
     }
-    if (tid == 0) J.s2_rec[t] = S2Agg{tot.d, min_rel, tot.w, tt == 0, S.strbytes};
-    __syncthreads();
+    __syncwarp();
+    tw.clear(W, lane);
+    if (lane == 0) J.s2_rec[t] = S2Agg{tw.depth, lo, tw.tape, tt == 0, sb};
   }
 }
 
 // ---------------------------------------------------------------------------
+// Stage-2 build: grammar, tape words, numbers and strings.
 __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ TileSmem S;
-  __shared__ uint64_t s_soff[kMaxTileTokens / 2];  // string-buffer offset of each string (list order)
-  const int tid = threadIdx.x;
+  __shared__ WarpSmem WS[kS2Warps];
+  const int lane = threadIdx.x & 31;
+  WarpSmem &W = WS[threadIdx.x >> 5];
+  for (uint32_t i = lane; i < 2 * kMaxTileTokens + 1; i += 32) W.open[i] = 0;
+  __syncwarp();
   const uint32_t n_tiles = J.counters[2];
   const uint32_t max_depth = J.max_depth;
-  for (uint32_t t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+  const uint32_t warps = gridDim.x * kS2Warps;
+  for (uint32_t t = blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -235,7 +282,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     const S2Agg agg = J.s2_rec[t];
     const uint64_t *front = J.front + ib + off + t;
 
-    if (tt == ntiles_d - 1 && tid == 0) {  // the document's last tile closes the tape
+    if (tt == ntiles_d - 1 && lane == 0) {  // the document's last tile closes the tape
       const int32_t d_end = pre.d_start + agg.dd;
       const uint64_t T = (uint64_t)pre.tape_start + agg.w + 1;
       if (d_end != 0) report(J, d, nidx, SJ_TAPE_ERROR);
@@ -247,150 +294,140 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       J.doc_str[d] = pre.str_start + agg.s;
     }
 
-    DW tot, ex;
-    uint32_t a, b;
-    tile_tokens(J, S, idxp, doc, len, off, cnt, nidx, tot, a, b, ex);
-
-    // string-buffer offsets of the tile's strings (token order)
-    if (tid < 32) {
-      uint64_t run = pre.str_start;
-      for (uint32_t base = 0; base < S.n_str; base += 32) {
-        const uint32_t i = base + tid;
-        uint64_t v = 0;
-        if (i < S.n_str) {
-          const uint32_t sl = J.slen[ib + off + S.list[i]];
-          v = 5ull + ((sl & 0x80000000u) ? 0 : sl);
-        }
-        uint64_t incl = v;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const uint64_t u = __shfl_up_sync(0xFFFFFFFFu, incl, o);
-          if (tid >= o) incl += u;
-        }
-        if (i < S.n_str) s_soff[i] = run + incl - v;
-        run += __shfl_sync(0xFFFFFFFFu, incl, 31);
-      }
+    const Staged sv = stage_tile(W, doc, len, (uint64_t)tt * kTileBytes, lane);
+    TileWalk tw;
+    tw.begin(idxp, off, cnt, nidx, len, lane);
+    // kinds of the two tokens before the tile
+    uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
+    if (lane < 2 && off >= (uint32_t)lane + 1) {
+      const uint8_t k = token_kind(doc[idxp[off - 1 - lane]]);
+      if (lane == 0) prev1 = k; else prev2 = k;
     }
-    __syncthreads();
+    prev1 = __shfl_sync(0xFFFFFFFFu, prev1, 0);
+    prev2 = __shfl_sync(0xFFFFFFFFu, prev2, 1);
+    uint64_t str_run = pre.str_start;
+    for (uint32_t base = 0; base < cnt; base += 32) {
+      Chunk c;
+      tw.next(c, W, sv, idxp, off, cnt, nidx, len, base, lane);
+      const uint8_t k = c.kind;
+      uint8_t p = __shfl_up_sync(0xFFFFFFFFu, k, 1);
+      uint8_t pp = __shfl_up_sync(0xFFFFFFFFu, k, 2);
+      if (lane == 0) { p = prev1; pp = prev2; }
+      if (lane == 1) pp = prev1;
+      prev2 = __shfl_sync(0xFFFFFFFFu, k, 30);
+      prev1 = __shfl_sync(0xFFFFFFFFu, k, 31);
+      // string-buffer offsets (token order)
+      uint32_t sl = 0;
+      if (c.valid && k == K_STRING) sl = J.slen[ib + off + c.j];
+      const uint64_t ssz = (c.valid && k == K_STRING) ? 5ull + ((sl & 0x80000000u) ? 0 : sl) : 0;
+      uint64_t sinc = ssz;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint64_t u = __shfl_up_sync(0xFFFFFFFFu, sinc, o);
+        if (lane >= o) sinc += u;
+      }
+      const uint64_t so = str_run + sinc - ssz;
+      str_run += __shfl_sync(0xFFFFFFFFu, sinc, 31);
+      if (!c.valid) continue;
 
-    // grammar and structure words, one token per thread at a time
-    {
-      int32_t pmin = min(0, ex.mn);
-      for (uint32_t j = a; j < b; j++) {
-        const uint64_t g = (uint64_t)off + j;
-        const uint8_t k = S.kind[j];
-        const int32_t Erel = j ? S.D[j - 1] : 0;
-        const int32_t E = pre.d_start + Erel;
-        const uint8_t p = j >= 1 ? S.kind[j - 1] : (g >= 1 ? token_kind(doc[idxp[g - 1]]) : K_OTHER);
-        const uint8_t pp = j >= 2 ? S.kind[j - 2] : (g >= 2 ? token_kind(doc[idxp[g - 2]]) : K_OTHER);
-        uint8_t K = 0;
-        uint64_t par_tape = ~0ull;
-        bool par_ok = true;
-        if (E >= 1) {
-          const int32_t pl = tile_parent(S, j, pmin);
-          if (pl >= 0) {
-            K = S.kind[pl];
-            par_tape = (uint64_t)pre.tape_start + S.tape[pl];
-          } else if (E >= max(1, pre.low) && E <= pre.d_start) {
-            const uint64_t ent = front[pre.d_start - E];
-            if (ent != ~0ull) {
-              K = (ent >> 63) ? K_OPEN_OBJ : K_OPEN_ARR;
-              par_tape = ent & 0xFFFFFFFFull;
-            } else {
-              par_ok = false;
-            }
+      const uint64_t g = (uint64_t)off + c.j;
+      const int32_t E = pre.d_start + c.E;
+      uint8_t K = 0;
+      uint64_t par_tape = ~0ull;
+      bool par_ok = true;
+      if (E >= 1) {
+        if (c.parent) {
+          K = (c.parent & 0x4000u) ? K_OPEN_OBJ : K_OPEN_ARR;
+          par_tape = (uint64_t)pre.tape_start + (c.parent & 0x0FFFu);
+        } else if (E >= max(1, pre.low) && E <= pre.d_start) {
+          const uint64_t ent = front[pre.d_start - E];
+          if (ent != ~0ull) {
+            K = (ent >> 63) ? K_OPEN_OBJ : K_OPEN_ARR;
+            par_tape = ent & 0xFFFFFFFFull;
           } else {
             par_ok = false;
           }
-        }
-        pmin = min(pmin, (int32_t)S.D[j]);
-        int code = 0;
-        if (E <= 0) {
-          if (!(g == 0 && is_value_start(k))) code = SJ_TAPE_ERROR;
-        } else if (!par_ok) {
-          code = SJ_TAPE_ERROR;
         } else {
-          const bool obj = K == K_OPEN_OBJ;
-          const bool value_end = p == K_NUMBER || is_atom(p) || is_close(p) ||
-                                 (p == K_STRING && (!obj || pp == K_COLON));
-          switch (k) {
-            case K_CLOSE_OBJ: if (!obj || !(p == K_OPEN_OBJ || value_end)) code = SJ_TAPE_ERROR; break;
-            case K_CLOSE_ARR: if (obj || !(p == K_OPEN_ARR || value_end)) code = SJ_TAPE_ERROR; break;
-            case K_COMMA: if (!value_end) code = SJ_TAPE_ERROR; break;
-            case K_COLON:
-              if (!(obj && p == K_STRING && (pp == K_OPEN_OBJ || pp == K_COMMA))) code = SJ_TAPE_ERROR;
-              break;
-            case K_STRING:
-              if (obj ? !(p == K_OPEN_OBJ || p == K_COMMA || p == K_COLON)
-                      : !(p == K_OPEN_ARR || p == K_COMMA))
-                code = SJ_TAPE_ERROR;
-              break;
-            case K_OTHER: code = SJ_TAPE_ERROR; break;
-            default:  // numbers, atoms, openers
-              if (obj ? p != K_COLON : !(p == K_OPEN_ARR || p == K_COMMA)) code = SJ_TAPE_ERROR;
-          }
+          par_ok = false;
         }
-        if (!code && is_open(k) && E + 1 > (int32_t)max_depth) code = SJ_DEPTH_ERROR;
-        const uint64_t tp = (uint64_t)pre.tape_start + S.tape[j];
-        const uint32_t pos = S.pos[j];
-        if (!code) {
-          if (is_close(k)) {
-            const uint64_t ot = par_tape;
-            if (tp < tape_cap && ot < tape_cap) {
-              tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | ot;
-              tape[ot] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
-            }
-          } else if (is_atom(k)) {
-            const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
-            const uint32_t n = k == K_FALSE ? 5 : 4;
-            bool ok = pos + n <= len;
-            for (uint32_t i = 0; ok && i < n; i++) ok = doc[pos + i] == (uint8_t)word[i];
-            if (ok && pos + n < len) ok = is_terminator(doc[pos + n]);
-            if (!ok) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR);
-            else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
-          } else if (k == K_NUMBER) {
-            const uint32_t i = atomicAdd(&S.n_num, 1u);
-            S.list[kMaxTileTokens - 1 - i] = (uint16_t)j;  // numbers fill the list from the end
-          } else if (k == K_STRING) {
-            const uint32_t sl = J.slen[ib + off + j];
-            if (sl & 0x80000000u) code = (int)(sl & 0xFF);
-          }
+      }
+      int code = 0;
+      if (E <= 0) {
+        if (!(g == 0 && is_value_start(k))) code = SJ_TAPE_ERROR;
+      } else if (!par_ok) {
+        code = SJ_TAPE_ERROR;
+      } else {
+        const bool obj = K == K_OPEN_OBJ;
+        const bool value_end = p == K_NUMBER || is_atom(p) || is_close(p) ||
+                               (p == K_STRING && (!obj || pp == K_COLON));
+        switch (k) {
+          case K_CLOSE_OBJ: if (!obj || !(p == K_OPEN_OBJ || value_end)) code = SJ_TAPE_ERROR; break;
+          case K_CLOSE_ARR: if (obj || !(p == K_OPEN_ARR || value_end)) code = SJ_TAPE_ERROR; break;
+          case K_COMMA: if (!value_end) code = SJ_TAPE_ERROR; break;
+          case K_COLON:
+            if (!(obj && p == K_STRING && (pp == K_OPEN_OBJ || pp == K_COMMA))) code = SJ_TAPE_ERROR;
+            break;
+          case K_STRING:
+            if (obj ? !(p == K_OPEN_OBJ || p == K_COMMA || p == K_COLON)
+                    : !(p == K_OPEN_ARR || p == K_COMMA))
+              code = SJ_TAPE_ERROR;
+            break;
+          case K_OTHER: code = SJ_TAPE_ERROR; break;
+          default:  // numbers, atoms, openers
+            if (obj ? p != K_COLON : !(p == K_OPEN_ARR || p == K_COMMA)) code = SJ_TAPE_ERROR;
         }
-        if (code) report(J, d, g, code);
       }
-    }
-    __syncthreads();
-
-    // numbers (Sec. 3.2.1), one per thread at a time
-    for (uint32_t i = tid; i < S.n_num; i += kS2Threads) {
-      const uint32_t j = S.list[kMaxTileTokens - 1 - i];
-      const uint64_t tp = (uint64_t)pre.tape_start + S.tape[j];
-      uint8_t tag;
-      uint64_t v;
-      const int code = parse_number(doc + S.pos[j], doc + len, tag, v);
-      if (code) report(J, d, (uint64_t)off + j, code);
-      else if (tp + 1 < tape_cap) {
-        tape[tp] = (uint64_t)tag << 56;
-        tape[tp + 1] = v;
+      if (!code && is_open(k) && E + 1 > (int32_t)max_depth) code = SJ_DEPTH_ERROR;
+      const uint64_t tp = (uint64_t)pre.tape_start + c.tape;
+      // Content is checked even where the grammar failed: a grammar code is
+      // smaller than any content code, so the minimum keeps the grammar first.
+      if (is_close(k)) {
+        if (!code && tp < tape_cap && par_tape < tape_cap) {
+          tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
+          tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
+        }
+      } else if (is_atom(k)) {
+        const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
+        const uint32_t n = k == K_FALSE ? 5 : 4;
+        bool ok = c.pos + n <= len;
+        for (uint32_t i = 0; ok && i < n; i++) ok = sv.at(c.pos + i) == (uint8_t)word[i];
+        if (ok && c.pos + n < len) ok = is_terminator(sv.at(c.pos + n));
+        if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
+        else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
+      } else if (k == K_NUMBER) {  // Sec. 3.2.1
+        uint8_t tag;
+        uint64_t v;
+        int nc;
+        const uint64_t p0 = c.pos, p1 = c.next;
+        if (p1 < sv.slimit || (p1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
+          const uint8_t *sp = sv.smem + (p0 - sv.sbase);
+          nc = parse_number(sp, sp + (min(len, sv.slimit) - p0), tag, v);
+        } else {
+          nc = parse_number(doc + p0, doc + len, tag, v);
+        }
+        if (nc) { if (!code) code = nc; }
+        else if (tp + 1 < tape_cap) {
+          tape[tp] = (uint64_t)tag << 56;
+          tape[tp + 1] = v;
+        }
+      } else if (k == K_STRING) {  // Sec. 3.2.2
+        if (sl & 0x80000000u) {
+          if (!code) code = (int)(sl & 0xFF);
+        } else if (tp < tape_cap && so + 5 + sl <= str_cap) {
+          tape[tp] = ((uint64_t)'"' << 56) | so;
+          uint8_t *o = strs + so;
+          o[0] = (uint8_t)sl; o[1] = (uint8_t)(sl >> 8); o[2] = (uint8_t)(sl >> 16); o[3] = (uint8_t)(sl >> 24);
+          int err;
+          const uint64_t p0 = (uint64_t)c.pos + 1, p1 = c.next;
+          const uint8_t *sp = sv.ptr(p0, p1);
+          string_walk<true>(sp, sp + (p1 - p0), err, o + 4);
+          o[4 + sl] = 0;
+        }
       }
+      if (code) report(J, d, g, code);
     }
-    // strings (Sec. 3.2.2): the '"' word and the (length, bytes, NUL) record
-    for (uint32_t i = tid; i < S.n_str; i += kS2Threads) {
-      const uint32_t j = S.list[i];
-      const uint32_t sl = J.slen[ib + off + j];
-      if (sl & 0x80000000u) continue;
-      const uint64_t tp = (uint64_t)pre.tape_start + S.tape[j];
-      const uint64_t so = s_soff[i];
-      if (tp < tape_cap && so + 5 + sl <= str_cap) {
-        tape[tp] = ((uint64_t)'"' << 56) | so;
-        uint8_t *o = strs + so;
-        o[0] = (uint8_t)sl; o[1] = (uint8_t)(sl >> 8); o[2] = (uint8_t)(sl >> 16); o[3] = (uint8_t)(sl >> 24);
-        int err;
-        string_walk<true>(doc + S.pos[j] + 1, doc + S.pos[j + 1], err, o + 4);
-        o[4 + sl] = 0;
-      }
-    }
-    __syncthreads();
+    __syncwarp();
+    tw.clear(W, lane);
   }
 }
 

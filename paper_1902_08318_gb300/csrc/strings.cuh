@@ -64,13 +64,32 @@ __device__ __forceinline__ uint32_t string_walk(const uint8_t *s, const uint8_t 
   const uint8_t *p = s;
   err = 0;
   for (;;) {
-    // plain runs, 4 bytes at a time where the address allows
-    while (p + 4 <= lim && (((uintptr_t)p) & 3) == 0) {
-      uint32_t x = *reinterpret_cast<const uint32_t *>(p);
-      if (special4(x)) break;
-      if (WRITE) { out[n] = (uint8_t)x; out[n + 1] = (uint8_t)(x >> 8); out[n + 2] = (uint8_t)(x >> 16); out[n + 3] = (uint8_t)(x >> 24); }
-      n += 4;
-      p += 4;
+    // plain runs, 4 bytes at a time: aligned word loads realigned with a
+    // funnel shift (a word holding a byte before `lim` lies in a page the
+    // document uses)
+    if (p + 4 <= lim) {
+      const uintptr_t ua = (uintptr_t)p;
+      const uint32_t *wp = reinterpret_cast<const uint32_t *>(ua & ~(uintptr_t)3);
+      const uint32_t sh = (uint32_t)(ua & 3) * 8;
+      uint32_t lo = sh ? wp[0] : 0u;  // holds byte p
+      while (p + 4 <= lim) {
+        uint32_t x, hi = 0;
+        if (sh) {
+          hi = wp[1];  // holds byte p + 3
+          x = __funnelshift_r(lo, hi, sh);
+        } else {
+          x = wp[0];
+        }
+        if (special4(x)) break;
+        if (WRITE) {
+          out[n] = (uint8_t)x; out[n + 1] = (uint8_t)(x >> 8);
+          out[n + 2] = (uint8_t)(x >> 16); out[n + 3] = (uint8_t)(x >> 24);
+        }
+        n += 4;
+        p += 4;
+        wp++;
+        lo = hi;
+      }
     }
     if (p >= lim) { err = SJ_STRING_ERROR; return n; }
     uint8_t c = *p;
