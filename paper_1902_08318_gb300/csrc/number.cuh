@@ -36,6 +36,32 @@ __device__ __forceinline__ bool is_terminator(uint8_t c) {
          c == '}' || c == '[' || c == '{';
 }
 
+// Eight ASCII bytes (little-endian in v) that are all decimal digits: every
+// high nibble is 3 and adding 6 to every byte leaves it so (low nibble <= 9).
+// The high-nibble test rules out bytes >= 0xF0, so the addition cannot carry
+// from one byte into the next.  (Sec. 3.2.1 checks eight digits at once.)
+__device__ __forceinline__ bool eight_digits(uint64_t v) {
+  const uint64_t hi = 0xF0F0F0F0F0F0F0F0ull, threes = 0x3030303030303030ull;
+  return (v & hi) == threes && ((v + 0x0606060606060606ull) & hi) == threes;
+}
+
+// Value of eight digits, first digit in the lowest byte: neighbouring digits
+// are combined into 2-, then 4-, then 8-digit numbers with one multiply and
+// one shift per step.
+__device__ __forceinline__ uint32_t eight_digit_value(uint64_t v) {
+  v -= 0x3030303030303030ull;
+  v = (v * 10 + (v >> 8)) & 0x00FF00FF00FF00FFull;
+  v = (v * 100 + (v >> 16)) & 0x0000FFFF0000FFFFull;
+  return (uint32_t)((v * 10000 + (v >> 32)) & 0xFFFFFFFFull);
+}
+
+__device__ __forceinline__ uint64_t load8(const uint8_t *p) {
+  uint64_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 8; k++) v |= (uint64_t)p[k] << (8 * k);
+  return v;
+}
+
 // ---------------------------------------------------------------------------
 // Exact comparison of a decimal with H * 2^g (big integers, rare path).
 // ---------------------------------------------------------------------------
@@ -253,6 +279,14 @@ __device__ __forceinline__ int parse_number(const uint8_t *s, const uint8_t *end
   if (*p == '0') {
     p++;
   } else {
+    // the first digit is 1-9, so w > 0 from here on and every digit counts
+    while (nw + 8 <= 19 && p + 8 <= end) {
+      const uint64_t v = load8(p);
+      if (!eight_digits(v)) break;
+      w = w * 100000000ull + eight_digit_value(v);
+      nw += 8;
+      p += 8;
+    }
     while (p < end && is_digit(*p)) {
       uint32_t d = *p - '0';
       if (nw < 19) { w = w * 10 + d; nw++; }
@@ -264,6 +298,14 @@ __device__ __forceinline__ int parse_number(const uint8_t *s, const uint8_t *end
     is_int = false;
     p++;
     if (p >= end || !is_digit(*p)) return SJ_NUMBER_ERROR;
+    while (w != 0 && nw + 8 <= 19 && p + 8 <= end) {
+      const uint64_t v = load8(p);
+      if (!eight_digits(v)) break;
+      w = w * 100000000ull + eight_digit_value(v);
+      nw += 8;
+      qa -= 8;
+      p += 8;
+    }
     while (p < end && is_digit(*p)) {
       uint32_t d = *p - '0';
       if (nw < 19) {

@@ -30,12 +30,38 @@ __device__ __forceinline__ uint64_t bs_run_before(const uint8_t *doc, uint64_t e
   }
 }
 
+// UTF-8 check of one 64-byte block whose words are in shared memory (a
+// compact loop: only non-ASCII words, or words continuing a sequence, are
+// walked byte by byte).  `prev` holds the 3 bytes before the block in its top
+// bytes, `nprev` of them inside the document.
+__device__ __noinline__ bool utf8_block_error_smem(const uint32_t *w, uint32_t prev, int nprev,
+                                                   bool doc_ends_here) {
+  Utf8State s{0, 0x80, 0xBF, false};
+  for (int k = 3 - nprev; k < 3; k++) {
+    Utf8State t = s;
+    utf8_step(t, (prev >> (8 * (k + 1))) & 0xFF);
+    if (t.err) t = Utf8State{0, 0x80, 0xBF, false};
+    s = t;
+  }
+#pragma unroll 1
+  for (int j = 0; j < 16; j++) {
+    const uint32_t x = w[j];
+    if ((x & 0x80808080u) == 0 && s.need == 0) continue;
+#pragma unroll 1
+    for (int b = 0; b < 4; b++) utf8_step(s, (x >> (8 * b)) & 0xFF);
+  }
+  if (doc_ends_here && s.need) s.err = true;
+  return s.err;
+}
+
 // How the byte before a tile makes its first byte a token start.
 enum : uint32_t { kSepNever = 0, kSepAlways = 1, kSepIfOutside = 2 };
 
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
+  __shared__ uint32_t s_words[kS1Warps * 32][17];  // one block per thread, padded
   const int lane = threadIdx.x & 31;
+  uint32_t *my_words = s_words[threadIdx.x];
   const uint32_t n_tiles = J.counters[2];
   const uint32_t warps = gridDim.x * kS1Warps;
   for (uint32_t t = blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
@@ -62,8 +88,11 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
       }
       const bool need = m.nonascii != 0 || (prev & (prev << 1) & 0x80808000u);
       const bool ends_here = blk < len && blk + 64 >= len;
-      if (blk < len && need && utf8_block_error(w, prev, nprev, ends_here))
-        atomicOr(&J.doc_flags[d], kFlagUtf8);
+      if (blk < len && need) {
+#pragma unroll
+        for (int k = 0; k < 16; k++) my_words[k] = w[k];
+        if (utf8_block_error_smem(my_words, prev, nprev, ends_here)) atomicOr(&J.doc_flags[d], kFlagUtf8);
+      }
     }
 
     // ---- carries read from the bytes before the tile --------------------------
