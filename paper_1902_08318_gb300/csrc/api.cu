@@ -54,6 +54,9 @@ struct sj_parser {
   sj::S2Agg *d_scan_pre = nullptr;
   int32_t *d_spt = nullptr;
   uint32_t *d_slen = nullptr;
+  ulonglong2 *d_s1_qx = nullptr;
+  uint64_t *d_meta = nullptr;
+  uint16_t *d_open_g = nullptr;
   uint64_t *d_front = nullptr;
   uint32_t *d_surv = nullptr;
   uint32_t *d_idx = nullptr;
@@ -71,7 +74,7 @@ struct sj_parser {
   uint64_t *h_doc_off = nullptr;
   sj_doc_result *h_results = nullptr;
   // launch shapes
-  int s1_grid = 0, s2_grid = 0, fin_grid = 0, aux_grid = 0;
+  int s1_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
   uint32_t scan_blocks = 0, spt_levels = 0;
   // graph cache
   cudaStream_t cap_stream = nullptr;
@@ -115,7 +118,8 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
                  p->d_tile_off, p->d_s1_rec, p->d_s1_pre, p->d_s1_blk, p->d_s2_rec, p->d_s2_pre,
                  p->d_scan_agg, p->d_scan_pre, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
-                 p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job};
+                 p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
+                 p->d_open_g};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_job) cudaFreeHost(p->h_job);
@@ -150,6 +154,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(&p->d_scan_pre, p->scan_blocks))) return r;
   if ((r = dalloc(&p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
   if ((r = dalloc(&p->d_slen, max_bytes + 16))) return r;
+  if ((r = dalloc(&p->d_s1_qx, tiles * 32))) return r;
+  if ((r = dalloc(&p->d_meta, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_front, max_bytes + tiles + 16))) return r;
   if ((r = dalloc(&p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_idx, max_bytes + 16))) return r;
@@ -170,13 +176,21 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
 
-  int sms = 0, occ1 = 0, occ2 = 0;
+  int sms = 0, occ1 = 0, occ2r = 0, occ2b = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_blocks_kernel,
                                                    32 * sj::kS1Warps, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2, sj::stage2_build_kernel, sj::kS2Threads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2r, sj::stage2_reduce_kernel,
+                                                   sj::kS2Threads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2b, sj::stage2_build_kernel,
+                                                   sj::kS2Threads, 0));
   p->s1_grid = sms * (occ1 > 0 ? occ1 : 1);
-  p->s2_grid = sms * (occ2 > 0 ? occ2 : 1);
+  p->s2r_grid = sms * (occ2r > 0 ? occ2r : 1);
+  p->s2b_grid = sms * (occ2b > 0 ? occ2b : 1);
+  // level tables of the reduce warps (zero between tiles)
+  const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
+  if ((r = dalloc(&p->d_open_g, open_entries))) return r;
+  CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
 
@@ -200,6 +214,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.spt_stride = (uint32_t)tiles;
   J.spt_levels = p->spt_levels;
   J.slen = p->d_slen;
+  J.s1_qx = p->d_s1_qx;
+  J.meta = p->d_meta;
+  J.open_g = p->d_open_g;
   J.front = p->d_front;
   J.surv = p->d_surv;
   J.idx = p->d_idx;
@@ -244,7 +261,7 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[3], s);
   sj::stage1_flatten_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
-  sj::stage2_reduce_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
   sj::launch_scan2(p->d_job, p->scan_blocks, s);
   for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
@@ -252,7 +269,7 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
-  sj::stage2_build_kernel<<<p->s2_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[7], s);
   sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);

@@ -139,6 +139,8 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
       cnt[h] = c;
     }
     reinterpret_cast<ulonglong2 *>(J.s1_blk)[(uint64_t)t * 32 + lane] = make_ulonglong2(S[0], S[1]);
+    // real quotes and string-special bytes (backslash, control) for stage 2
+    J.s1_qx[(uint64_t)t * 32 + lane] = make_ulonglong2(Q, m.bs | ctrl_mask(w));
     if (lane == 0) {
       S1Agg a;
       a.qpar = __popc(pb) & 1u;

@@ -70,6 +70,19 @@ __device__ __forceinline__ void classify_block(const uint32_t (&w)[16], BlockMas
   m.nonascii = na & 0x80808080u;
 }
 
+// Bytes below 0x20 of a block (exact per byte: with the top three bits kept,
+// a byte is zero exactly when it was a control character).
+__device__ __forceinline__ uint64_t ctrl_mask(const uint32_t (&w)[16]) {
+  uint32_t r[2] = {0, 0};
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const uint32_t t = w[j] & 0xE0E0E0E0u;
+    const uint32_t z = ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
+    r[j >> 3] |= movemask4(z) << ((j & 7) * 4);
+  }
+  return ((uint64_t)r[1] << 32) | r[0];
+}
+
 // ---------------------------------------------------------------------------
 // Fig. "identifyescapedquotes": bytes that follow an odd-length backslash run,
 // assuming no run is carried in.  The carried-in case differs only at the

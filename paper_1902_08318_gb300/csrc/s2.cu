@@ -32,30 +32,31 @@ __device__ __forceinline__ void report(const Job &J, uint32_t d, uint64_t token,
 constexpr int kS2Warps = kS2Threads / 32;
 constexpr int kHalo = 1024;                    // staged bytes past the tile's end
 constexpr int kStageBytes = kTileBytes + kHalo;
+constexpr int kStageBlocks = kStageBytes / kBlockBytes;
 constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
+constexpr int kOpenSmem = 1024;                // levels kept in shared memory (mod 1024)
+constexpr int kStrStage = 3328;                // string output of one chunk, staged
 
-// Per-warp shared state.  `open[l]` is the container currently open at
-// relative level l (levels are depths after an opener, relative to the tile
-// start), written by openers of this tile: 0 = none, else bit 15 set,
-// bit 14 = object, bits 0-11 = the opener's tape slot relative to the tile.
-struct __align__(16) WarpSmem {  // 16-byte aligned size: bytes[] of every warp takes uint4 stores
-  uint8_t bytes[kStageBytes + 64];
-  uint16_t open[2 * kMaxTileTokens + 1];
-};
-static_assert(sizeof(WarpSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+// A string's entry in `slen`: an error code, or its normalised length and
+// whether it holds escapes (then the build pass walks it again).
+constexpr uint32_t kSlenErr = 0x80000000u, kSlenWalk = 0x40000000u, kSlenLen = 0x3FFFFFFFu;
+
+// Token facts passed from the reduce pass to the build pass, one word per
+// token: kind (4 bits), depth before the token relative to the tile (13 bits,
+// biased by 4096), tape slot relative to the tile (13), the enclosing
+// container when it was opened in the tile (16: bit 15 valid, bit 14 object,
+// bits 0-11 its tape slot), and the string-buffer offset relative to the
+// tile (18).
+__device__ __forceinline__ uint64_t pack_meta(uint32_t kind, int32_t E, uint32_t tape,
+                                              uint32_t parent, uint32_t srel) {
+  return (uint64_t)kind | ((uint64_t)(uint32_t)(E + 4096) << 4) | ((uint64_t)tape << 17) |
+         ((uint64_t)parent << 30) | ((uint64_t)srel << 46);
+}
 
 __device__ __forceinline__ uint32_t warp_incl_u32(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
-    if (lane >= o) v += u;
-  }
-  return v;
-}
-__device__ __forceinline__ int32_t warp_incl_i32(int32_t v, int lane) {
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
     if (lane >= o) v += u;
   }
   return v;
@@ -77,7 +78,8 @@ struct Staged {
   }
 };
 
-__device__ __forceinline__ Staged stage_tile(WarpSmem &W, const uint8_t *doc, uint64_t len,
+// Copy the tile's bytes and kHalo more (16-byte chunks) into shared memory.
+__device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc, uint64_t len,
                                              uint64_t t0, int lane) {
   const uintptr_t g0 = (uintptr_t)(doc + t0);
   const uintptr_t a0 = g0 & ~(uintptr_t)15;
@@ -85,180 +87,279 @@ __device__ __forceinline__ Staged stage_tile(WarpSmem &W, const uint8_t *doc, ui
   const uintptr_t send = min((uintptr_t)(a0 + kStageBytes), dend);
   const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
   for (uint32_t c = lane; c < nch; c += 32)
-    reinterpret_cast<uint4 *>(W.bytes)[c] = __ldg(reinterpret_cast<const uint4 *>(a0 + 16 * c));
+    reinterpret_cast<uint4 *>(bytes)[c] = __ldg(reinterpret_cast<const uint4 *>(a0 + 16 * c));
   __syncwarp();
   Staged v;
   v.doc = doc;
   v.len = len;
   v.sbase = (int64_t)t0 - (int64_t)(g0 - a0);
   v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
-  v.smem = W.bytes;
+  v.smem = bytes;
   return v;
 }
 
-// Tokens of one tile, 32 at a time: positions, kinds, depths, tape slots and
-// the enclosing container of each token (from the warp's level table, or -1
-// when it was opened before the tile).
-struct Chunk {
-  uint32_t j;       // token index in the tile
-  bool valid;
-  uint32_t pos, next;
-  uint8_t kind;
-  int32_t E, D;     // relative depth before / after the token
-  uint32_t tape;    // relative tape slot
-  uint32_t sord;    // string ordinal in the tile (strings before this token)
-  uint16_t parent;  // open[] entry of the enclosing container, 0 = before the tile
-};
-
-struct TileWalk {
-  int32_t depth = 0, dmin = 0, dmax = 0;
-  uint32_t tape = 0, nstr = 0;
-  uint32_t pos_next = 0;  // first position of the next chunk
-
-  __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt,
-                                        uint32_t nidx, uint64_t len, int lane) {
-    const uint32_t j = lane;
-    pos_next = j < cnt ? idxp[off + j] : 0u;
-    (void)nidx;
-    (void)len;
+// Position of the token after each token of a chunk (the next index, or the
+// document's end after its last token), with the next chunk prefetched.
+struct Positions {
+  uint32_t pos_next = 0;
+  __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt, int lane) {
+    pos_next = (uint32_t)lane < cnt ? idxp[off + lane] : 0u;
   }
-
-  __device__ __forceinline__ void next(Chunk &c, WarpSmem &W, const Staged &sv, const uint32_t *idxp,
+  __device__ __forceinline__ void next(uint32_t &pos, uint32_t &nxt, const uint32_t *idxp,
                                        uint32_t off, uint32_t cnt, uint32_t nidx, uint64_t len,
                                        uint32_t base, int lane) {
-    c.j = base + lane;
-    c.valid = c.j < cnt;
-    c.pos = pos_next;
-    // prefetch the next chunk
-    const uint32_t jn = base + 32 + lane;
+    const uint32_t j = base + lane;
+    pos = pos_next;
+    const uint32_t jn = j + 32;
     pos_next = jn < cnt ? idxp[off + jn] : 0u;
-    uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, c.pos, 1);
+    uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, pos, 1);
     const uint32_t first_next = __shfl_sync(0xFFFFFFFFu, pos_next, 0);
-    if (lane == 31 || c.j + 1 == cnt) {
-      const uint32_t g = off + c.j + 1;  // document index of the next token
-      nx = (c.j + 1 < cnt) ? first_next : (g < nidx ? idxp[g] : (uint32_t)len);
+    if (lane == 31 || j + 1 == cnt) {
+      const uint32_t g = off + j + 1;  // document index of the next token
+      nx = (j + 1 < cnt) ? first_next : (g < nidx ? idxp[g] : (uint32_t)len);
     }
-    c.next = nx;
-    c.kind = c.valid ? token_kind(sv.at(c.pos)) : K_OTHER;
-    const int32_t dl = c.valid ? depth_delta(c.kind) : 0;
-    const int32_t di = warp_incl_i32(dl, lane);
-    c.D = depth + di;
-    c.E = c.D - dl;
-    const uint32_t w = c.valid ? tape_words_of(c.kind) : 0u;
-    const uint32_t wi = warp_incl_u32(w, lane);
-    c.tape = tape + wi - w;
-    const uint32_t si = __ballot_sync(0xFFFFFFFFu, c.valid && c.kind == K_STRING);
-    c.sord = nstr + __popc(si & ((1u << lane) - 1u));
-    // parents: the last opener of this chunk at the token's level, else the table
-    const bool op = c.valid && is_open(c.kind);
-    uint16_t my = op ? (uint16_t)(0x8000u | (c.kind == K_OPEN_OBJ ? 0x4000u : 0u) | c.tape) : 0;
-    c.parent = 0;
-    unsigned pending = __ballot_sync(0xFFFFFFFFu, c.valid);
-    const unsigned below = (1u << lane) - 1u;
-    while (pending) {
-      const int32_t lv = __shfl_sync(0xFFFFFFFFu, c.E, __ffs(pending) - 1);
-      const unsigned opl = __ballot_sync(0xFFFFFFFFu, op && c.D == lv);
-      const bool mine = ((pending >> lane) & 1u) && c.E == lv;
-      const unsigned m = opl & below;
-      const int src = (mine && m) ? 31 - __clz(m) : lane;
-      const uint16_t got = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, src);
-      if (mine) {
-        if (m) c.parent = got;
-        else if (lv > -kLevelOff && lv <= kLevelOff) c.parent = W.open[lv + kLevelOff];
-      }
-      pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
-    }
-    // the last opener of each level of this chunk stays open for later tokens
-    const unsigned grp = __match_any_sync(0xFFFFFFFFu, op ? c.D : 0x7FFFFFFF);
-    if (op && lane == 31 - __clz(grp)) W.open[c.D + kLevelOff] = my;
-    // advance
-    depth += __shfl_sync(0xFFFFFFFFu, di, 31);
-    tape += __shfl_sync(0xFFFFFFFFu, wi, 31);
-    nstr += __popc(si);
-    int32_t mn = c.valid ? min(c.E, c.D) : 0x7FFFFFFF, mx = c.valid ? max(c.E, c.D) : -0x7FFFFFFF;
-#pragma unroll
-    for (int o = 16; o; o >>= 1) {
-      mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
-      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-    }
-    dmin = min(dmin, mn);
-    dmax = max(dmax, mx);
-    __syncwarp();
-  }
-
-  // forget this tile's levels
-  __device__ __forceinline__ void clear(WarpSmem &W, int lane) {
-    for (int32_t v = max(dmin, -kLevelOff) + lane; v <= min(dmax, kLevelOff); v += 32)
-      W.open[v + kLevelOff] = 0;
-    __syncwarp();
+    nxt = nx;
   }
 };
 
 // ---------------------------------------------------------------------------
 // Stage-2 reduce: per tile, the depth change and lowest depth, tape words,
-// string-buffer bytes (string lengths are stored for the build pass), and the
-// containers left open at each level (the survivors).
+// string-buffer bytes, and the containers left open at each level (the
+// survivors); per token, the facts the build pass needs (pack_meta) and the
+// normalised length of each string.
+// ---------------------------------------------------------------------------
+struct __align__(16) ReduceSmem {  // 16-byte aligned size: bytes[] takes uint4 stores
+  uint8_t bytes[kStageBytes + 64];
+  uint64_t q[kStageBlocks];        // real quotes of the staged blocks
+  uint64_t x[kStageBlocks];        // backslash and control bytes of the staged blocks
+  uint16_t open[kOpenSmem];
+};
+static_assert(sizeof(ReduceSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
+
+// `open` entry of relative level l: the container currently open there, written
+// by the openers of the tile (0 = none, else bit 15, bit 14 = object, bits
+// 0-11 = the opener's tape slot relative to the tile).  A tile with fewer than
+// 1024 tokens spans fewer than 1024 levels, so they fit in shared memory
+// modulo 1024; other tiles use the warp's table in global memory.
+struct OpenTable {
+  uint16_t *p;
+  uint32_t mask;
+  int32_t bias;
+  __device__ __forceinline__ uint16_t &at(int32_t l) const { return p[(uint32_t)(l + bias) & mask]; }
+};
+
+// Normalised length of a string without escapes or control bytes, from the
+// staged masks: the distance from its first content byte (document position
+// p0) to the next real quote.  False when the masks cannot decide it.
+__device__ __forceinline__ bool plain_string_len(const ReduceSmem &W, uint64_t t0, uint64_t p0,
+                                                 uint32_t nblk, uint32_t &L) {
+  const uint32_t rel = (uint32_t)(p0 - t0);
+  uint32_t w = rel >> 6, b = rel & 63, acc = 0;
+  while (w < nblk) {
+    const uint64_t q = W.q[w] >> b, x = W.x[w] >> b;
+    if (q) {
+      const uint32_t z = (uint32_t)__ffsll((long long)q) - 1;
+      if (x & ((1ull << z) - 1)) return false;
+      L = acc + z;
+      return true;
+    }
+    if (x) return false;
+    acc += 64 - b;
+    b = 0;
+    w++;
+  }
+  return false;
+}
+
 __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ WarpSmem WS[kS2Warps];
+  __shared__ ReduceSmem WS[kS2Warps];
+  __shared__ uint8_t s_kind[256];
+  for (uint32_t i = threadIdx.x; i < 256; i += blockDim.x) s_kind[i] = token_kind((uint8_t)i);
   const int lane = threadIdx.x & 31;
-  WarpSmem &W = WS[threadIdx.x >> 5];
-  for (uint32_t i = lane; i < 2 * kMaxTileTokens + 1; i += 32) W.open[i] = 0;
-  __syncwarp();
+  const uint32_t wid = threadIdx.x >> 5;
+  ReduceSmem &W = WS[wid];
+  for (uint32_t i = lane; i < kOpenSmem; i += 32) W.open[i] = 0;
+  __syncthreads();
+  uint16_t *const open_g = J.open_g + (uint64_t)(blockIdx.x * kS2Warps + wid) * kOpenGlobal;
   const uint32_t n_tiles = J.counters[2];
   const uint32_t warps = gridDim.x * kS2Warps;
-  for (uint32_t t = blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  const unsigned below = (1u << lane) - 1u;
+  for (uint32_t t = blockIdx.x * kS2Warps + wid; t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
-    const uint32_t tt = t - J.tile_first[d];
+    const uint32_t j_min = J.tile_first[d];
+    const uint32_t tt = t - j_min;
     const uint32_t nidx = J.doc_nidx[d];
     if ((J.doc_flags[d] & kDocBad) || nidx == 0) {
       if (lane == 0) J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
       continue;
     }
+    const uint32_t ntiles_d = J.tile_first[d + 1] - j_min;
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
     const uint8_t *doc = J.base + J.doc_off[d];
     const uint64_t ib = idx_base(J, d);
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
-    const Staged sv = stage_tile(W, doc, len, (uint64_t)tt * kTileBytes, lane);
-    TileWalk tw;
-    tw.begin(idxp, off, cnt, nidx, len, lane);
+    const uint64_t t0 = (uint64_t)tt * kTileBytes;
+    // masks of the tile's blocks and of the next ones in the document
+    const uint32_t nblk = min((uint32_t)kStageBlocks, (ntiles_d - tt) * 32u);
+    for (uint32_t k = lane; k < nblk; k += 32) {
+      const ulonglong2 v = J.s1_qx[(uint64_t)t * 32 + k];
+      W.q[k] = v.x;
+      W.x[k] = v.y;
+    }
+    const Staged sv = stage_tile(W.bytes, doc, len, t0, lane);
+    const OpenTable ot = cnt < (uint32_t)kOpenSmem ? OpenTable{W.open, (uint32_t)kOpenSmem - 1u, 0}
+                                                   : OpenTable{open_g, 0xFFFFFFFFu, kLevelOff};
+    Positions ps;
+    ps.begin(idxp, off, cnt, lane);
+    int32_t depth = 0, mn = 0, mx = 0;
+    uint32_t tape = 0, srun = 0;
     uint64_t sb = 0;
     for (uint32_t base = 0; base < cnt; base += 32) {
-      Chunk c;
-      tw.next(c, W, sv, idxp, off, cnt, nidx, len, base, lane);
-      if (c.valid && c.kind == K_STRING) {  // normalised length (Sec. 3.2.2)
-        int err;
-        const uint64_t p0 = (uint64_t)c.pos + 1, p1 = c.next;
-        const uint8_t *sp = sv.ptr(p0, p1);
-        const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
-        J.slen[ib + off + c.j] = err ? (0x80000000u | (uint32_t)err) : n;
-        sb += 5ull + (err ? 0 : n);
+      const uint32_t j = base + lane;
+      const bool valid = j < cnt;
+      uint32_t pos, nxt;
+      ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
+      const uint8_t kind = valid ? s_kind[sv.smem[pos - sv.sbase]] : K_OTHER;
+      // depth and tape slot: one scan over (delta + 1) | words << 8
+      const int32_t dl = depth_delta(kind);
+      const uint32_t w = tape_words_of(kind);
+      const uint32_t vi = warp_incl_u32((uint32_t)(dl + 1) | (w << 8), lane);
+      const int32_t D = depth + (int32_t)(vi & 0xFFu) - (lane + 1);
+      const int32_t E = D - dl;
+      const uint32_t tp = tape + (vi >> 8) - w;
+      // enclosing container: the last opener of this chunk at the token's
+      // level, else the level table
+      const bool op = valid && is_open(kind);
+      const uint16_t my = op ? (uint16_t)(0x8000u | (kind == K_OPEN_OBJ ? 0x4000u : 0u) | tp) : 0;
+      uint16_t parent = 0;
+      unsigned pending = __ballot_sync(0xFFFFFFFFu, valid);
+      while (pending) {
+        const int32_t lv = __shfl_sync(0xFFFFFFFFu, E, __ffs(pending) - 1);
+        const unsigned opl = __ballot_sync(0xFFFFFFFFu, op && D == lv);
+        const bool mine = ((pending >> lane) & 1u) && E == lv;
+        const unsigned m = opl & below;
+        const int src = (mine && m) ? 31 - __clz(m) : lane;
+        const uint16_t got = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, src);
+        if (mine) {
+          if (m) parent = got;
+          else if (lv > -kLevelOff && lv <= kLevelOff) parent = ot.at(lv);
+        }
+        pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
       }
+      // the last opener of each level of this chunk stays open for later tokens
+      const unsigned grp = __match_any_sync(0xFFFFFFFFu, op ? D : 0x7FFFFFFF);
+      if (op && lane == 31 - __clz(grp)) ot.at(D) = my;
+      // strings: normalised length (Sec. 3.2.2)
+      uint32_t enc = 0, ssz = 0;
+      if (valid && kind == K_STRING) {
+        const uint64_t p0 = (uint64_t)pos + 1;
+        uint32_t L;
+        if (plain_string_len(W, t0, p0, nblk, L)) {
+          enc = L;
+          ssz = 5u + L;
+        } else {
+          int err;
+          const uint64_t p1 = nxt;
+          const uint8_t *sp = sv.ptr(p0, p1);
+          const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
+          if (err) {
+            enc = kSlenErr | (uint32_t)err;
+            ssz = 5u;
+          } else {
+            enc = kSlenWalk | min(n, kSlenLen);
+            ssz = 5u + n;
+          }
+        }
+        sb += ssz;
+      }
+      const uint32_t si = warp_incl_u32(ssz, lane);
+      const uint32_t srel = srun + si - ssz;
+      if (valid) {
+        J.meta[ib + off + j] = pack_meta(kind, E, tp, parent, srel);
+        if (kind == K_STRING) J.slen[ib + off + j] = enc;
+        mn = min(mn, min(E, D));
+        mx = max(mx, max(E, D));
+      }
+      const uint32_t tot = __shfl_sync(0xFFFFFFFFu, vi, 31);
+      depth += (int32_t)(tot & 0xFFu) - 32;
+      tape += tot >> 8;
+      srun += __shfl_sync(0xFFFFFFFFu, si, 31);
+      __syncwarp();
     }
 #pragma unroll
-    for (int o = 16; o; o >>= 1) sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
-    // survivors: the open container of each level in (dmin, depth]
-    const int32_t lo = tw.dmin;
-    for (int32_t lv = lo + 1 + lane; lv <= tw.depth; lv += 32) {
-      const uint16_t e = W.open[lv + kLevelOff];
-      J.surv[ib + off + (uint32_t)(lv - lo - 1)] = ((uint32_t)(e >> 14) & 1u) << 31 | (e & 0x0FFFu);
+    for (int o = 16; o; o >>= 1) {
+      sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
+      mn = min(mn, __shfl_xor_sync(0xFFFFFFFFu, mn, o));
+      mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+    }
+    // survivors: the open container of each level in (mn, depth]
+    for (int32_t lv = mn + 1 + lane; lv <= depth; lv += 32) {
+      const uint16_t e = ot.at(lv);
+      J.surv[ib + off + (uint32_t)(lv - mn - 1)] = ((uint32_t)(e >> 14) & 1u) << 31 | (e & 0x0FFFu);
     }
     __syncwarp();
-    tw.clear(W, lane);
-    if (lane == 0) J.s2_rec[t] = S2Agg{tw.depth, lo, tw.tape, tt == 0, sb};
+    // forget this tile's levels
+    for (int32_t v = max(mn, -kLevelOff) + lane; v <= min(mx, kLevelOff); v += 32) ot.at(v) = 0;
+    __syncwarp();
+    if (lane == 0) J.s2_rec[t] = S2Agg{depth, mn, tape, tt == 0, sb};
   }
 }
 
 // ---------------------------------------------------------------------------
 // Stage-2 build: grammar, tape words, numbers and strings.
+// ---------------------------------------------------------------------------
+struct __align__(16) BuildSmem {
+  uint8_t bytes[kStageBytes + 64];
+  uint8_t sout[kStrStage];  // the string-buffer bytes of one chunk, before a coalesced copy
+};
+static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
+              "per-warp staging must stay 16-byte aligned");
+
+// Grammar (Sec. 3.2, RFC 8259): which previous tokens may precede a token of
+// kind k inside an object (obj) or an array.  Bit c of the row is the class
+// of the previous token: its kind, or kKeyStr for a string that is an object
+// key.
+constexpr uint32_t kKeyStr = 12;
+__device__ __forceinline__ uint16_t grammar_row(uint32_t k, bool obj) {
+  const uint32_t value_end = (1u << K_NUMBER) | (1u << K_TRUE) | (1u << K_FALSE) | (1u << K_NULL) |
+                             (1u << K_CLOSE_OBJ) | (1u << K_CLOSE_ARR) | (1u << K_STRING);
+  const uint32_t elem = (1u << K_OPEN_ARR) | (1u << K_COMMA);  // a value starts in an array
+  switch (k) {
+    case K_CLOSE_OBJ: return (uint16_t)(obj ? ((1u << K_OPEN_OBJ) | value_end) : 0u);
+    case K_CLOSE_ARR: return (uint16_t)(obj ? 0u : ((1u << K_OPEN_ARR) | value_end));
+    case K_COMMA: return (uint16_t)value_end;
+    case K_COLON: return (uint16_t)(obj ? (1u << kKeyStr) : 0u);
+    case K_STRING:
+      return (uint16_t)(obj ? ((1u << K_OPEN_OBJ) | (1u << K_COMMA) | (1u << K_COLON)) : elem);
+    case K_OPEN_OBJ: case K_OPEN_ARR: case K_NUMBER: case K_TRUE: case K_FALSE: case K_NULL:
+      return (uint16_t)(obj ? (1u << K_COLON) : elem);
+    default: return 0;
+  }
+}
+
+// Write one string's buffer entry (u32 length, bytes, NUL) at o.
+__device__ __forceinline__ void put_string(uint8_t *o, uint32_t n, bool walk, const uint8_t *sp,
+                                           const uint8_t *lim) {
+  o[0] = (uint8_t)n; o[1] = (uint8_t)(n >> 8); o[2] = (uint8_t)(n >> 16); o[3] = (uint8_t)(n >> 24);
+  if (walk) {
+    int err;
+    string_walk<true>(sp, lim, err, o + 4);
+  } else {
+    for (uint32_t i = 0; i < n; i++) o[4 + i] = sp[i];
+  }
+  o[4 + n] = 0;
+}
+
 __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ WarpSmem WS[kS2Warps];
+  __shared__ BuildSmem WS[kS2Warps];
+  __shared__ uint16_t s_gram[32];
+  if (threadIdx.x < 32) s_gram[threadIdx.x] = grammar_row(threadIdx.x >> 1, threadIdx.x & 1);
+  __syncthreads();
   const int lane = threadIdx.x & 31;
-  WarpSmem &W = WS[threadIdx.x >> 5];
-  for (uint32_t i = lane; i < 2 * kMaxTileTokens + 1; i += 32) W.open[i] = 0;
-  __syncwarp();
+  BuildSmem &W = WS[threadIdx.x >> 5];
   const uint32_t n_tiles = J.counters[2];
   const uint32_t max_depth = J.max_depth;
   const uint32_t warps = gridDim.x * kS2Warps;
@@ -279,10 +380,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     const uint64_t str_cap = str_base(J, d + 1) - str_base(J, d);
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
     const S2Pre pre = J.s2_pre[t];
-    const S2Agg agg = J.s2_rec[t];
     const uint64_t *front = J.front + ib + off + t;
 
     if (tt == ntiles_d - 1 && lane == 0) {  // the document's last tile closes the tape
+      const S2Agg agg = J.s2_rec[t];
       const int32_t d_end = pre.d_start + agg.dd;
       const uint64_t T = (uint64_t)pre.tape_start + agg.w + 1;
       if (d_end != 0) report(J, d, nidx, SJ_TAPE_ERROR);
@@ -294,51 +395,44 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       J.doc_str[d] = pre.str_start + agg.s;
     }
 
-    const Staged sv = stage_tile(W, doc, len, (uint64_t)tt * kTileBytes, lane);
-    TileWalk tw;
-    tw.begin(idxp, off, cnt, nidx, len, lane);
+    const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
+    Positions ps;
+    ps.begin(idxp, off, cnt, lane);
     // kinds of the two tokens before the tile
     uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
     if (lane < 2 && off >= (uint32_t)lane + 1) {
-      const uint8_t k = token_kind(doc[idxp[off - 1 - lane]]);
+      const uint8_t k = (uint8_t)(J.meta[ib + off - 1 - lane] & 15u);
       if (lane == 0) prev1 = k; else prev2 = k;
     }
     prev1 = __shfl_sync(0xFFFFFFFFu, prev1, 0);
     prev2 = __shfl_sync(0xFFFFFFFFu, prev2, 1);
-    uint64_t str_run = pre.str_start;
     for (uint32_t base = 0; base < cnt; base += 32) {
-      Chunk c;
-      tw.next(c, W, sv, idxp, off, cnt, nidx, len, base, lane);
-      const uint8_t k = c.kind;
+      const uint32_t j = base + lane;
+      const bool valid = j < cnt;
+      uint32_t pos, nxt;
+      ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
+      const uint64_t meta = valid ? J.meta[ib + off + j] : 0ull;
+      const uint8_t k = (uint8_t)(meta & 15u);
+      const int32_t E = pre.d_start + ((int32_t)((meta >> 4) & 0x1FFFu) - 4096);
+      const uint64_t tp = (uint64_t)pre.tape_start + ((meta >> 17) & 0x1FFFu);
+      const uint32_t parent = (uint32_t)(meta >> 30) & 0xFFFFu;
+      const uint64_t so = pre.str_start + (meta >> 46);
       uint8_t p = __shfl_up_sync(0xFFFFFFFFu, k, 1);
       uint8_t pp = __shfl_up_sync(0xFFFFFFFFu, k, 2);
       if (lane == 0) { p = prev1; pp = prev2; }
       if (lane == 1) pp = prev1;
       prev2 = __shfl_sync(0xFFFFFFFFu, k, 30);
       prev1 = __shfl_sync(0xFFFFFFFFu, k, 31);
-      // string-buffer offsets (token order)
-      uint32_t sl = 0;
-      if (c.valid && k == K_STRING) sl = J.slen[ib + off + c.j];
-      const uint64_t ssz = (c.valid && k == K_STRING) ? 5ull + ((sl & 0x80000000u) ? 0 : sl) : 0;
-      uint64_t sinc = ssz;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint64_t u = __shfl_up_sync(0xFFFFFFFFu, sinc, o);
-        if (lane >= o) sinc += u;
-      }
-      const uint64_t so = str_run + sinc - ssz;
-      str_run += __shfl_sync(0xFFFFFFFFu, sinc, 31);
-      if (!c.valid) continue;
+      const uint64_t g = (uint64_t)off + j;
 
-      const uint64_t g = (uint64_t)off + c.j;
-      const int32_t E = pre.d_start + c.E;
+      // ---- grammar: the enclosing container and the previous two tokens ----
       uint8_t K = 0;
       uint64_t par_tape = ~0ull;
       bool par_ok = true;
       if (E >= 1) {
-        if (c.parent) {
-          K = (c.parent & 0x4000u) ? K_OPEN_OBJ : K_OPEN_ARR;
-          par_tape = (uint64_t)pre.tape_start + (c.parent & 0x0FFFu);
+        if (parent) {
+          K = (parent & 0x4000u) ? K_OPEN_OBJ : K_OPEN_ARR;
+          par_tape = (uint64_t)pre.tape_start + (parent & 0x0FFFu);
         } else if (E >= max(1, pre.low) && E <= pre.d_start) {
           const uint64_t ent = front[pre.d_start - E];
           if (ent != ~0ull) {
@@ -358,27 +452,56 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         code = SJ_TAPE_ERROR;
       } else {
         const bool obj = K == K_OPEN_OBJ;
-        const bool value_end = p == K_NUMBER || is_atom(p) || is_close(p) ||
-                               (p == K_STRING && (!obj || pp == K_COLON));
-        switch (k) {
-          case K_CLOSE_OBJ: if (!obj || !(p == K_OPEN_OBJ || value_end)) code = SJ_TAPE_ERROR; break;
-          case K_CLOSE_ARR: if (obj || !(p == K_OPEN_ARR || value_end)) code = SJ_TAPE_ERROR; break;
-          case K_COMMA: if (!value_end) code = SJ_TAPE_ERROR; break;
-          case K_COLON:
-            if (!(obj && p == K_STRING && (pp == K_OPEN_OBJ || pp == K_COMMA))) code = SJ_TAPE_ERROR;
-            break;
-          case K_STRING:
-            if (obj ? !(p == K_OPEN_OBJ || p == K_COMMA || p == K_COLON)
-                    : !(p == K_OPEN_ARR || p == K_COMMA))
-              code = SJ_TAPE_ERROR;
-            break;
-          case K_OTHER: code = SJ_TAPE_ERROR; break;
-          default:  // numbers, atoms, openers
-            if (obj ? p != K_COLON : !(p == K_OPEN_ARR || p == K_COMMA)) code = SJ_TAPE_ERROR;
-        }
+        const uint32_t pc = (p == K_STRING && obj && pp != K_COLON) ? kKeyStr : p;
+        if (!((s_gram[(k << 1) | (obj ? 1 : 0)] >> pc) & 1u)) code = SJ_TAPE_ERROR;
       }
       if (!code && is_open(k) && E + 1 > (int32_t)max_depth) code = SJ_DEPTH_ERROR;
-      const uint64_t tp = (uint64_t)pre.tape_start + c.tape;
+
+      // ---- strings (Sec. 3.2.2): one chunk's entries are contiguous in the
+      //      buffer; stage them in shared memory and copy them out coalesced ----
+      const uint32_t sl = (valid && k == K_STRING) ? J.slen[ib + off + j] : 0u;
+      const bool is_str = valid && k == K_STRING && !(sl & kSlenErr);
+      if (valid && k == K_STRING && (sl & kSlenErr) && !code) code = (int)(sl & 0xFFu);
+      const bool walk = (sl & kSlenWalk) != 0;
+      const uint64_t p0 = (uint64_t)pos + 1;
+      uint64_t n = sl & kSlenLen;
+      if (is_str && n == kSlenLen) {  // too long for the entry: measure again
+        int err;
+        n = string_walk<false>(doc + p0, doc + nxt, err, nullptr);
+      }
+      const uint64_t src_end = walk ? (uint64_t)nxt : p0 + n;
+      const bool fits = !is_str || (n < kSlenLen && src_end <= sv.slimit);
+      const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
+      if (sm) {
+        const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
+        const uint64_t so_lo = __shfl_sync(0xFFFFFFFFu, so, __ffs(sm) - 1);
+        const uint64_t so_hi = __shfl_sync(0xFFFFFFFFu, so + 5 + n, 31 - __clz(sm));
+        const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
+        const uint64_t total = a + (so_hi - so_lo);
+        if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
+          if (is_str) {
+            const uint8_t *sp = sv.smem + (p0 - sv.sbase);
+            put_string(W.sout + a + (so - so_lo), (uint32_t)n, walk, sp, sp + (nxt - p0));
+          }
+          __syncwarp();
+          uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
+          const uint32_t units = (uint32_t)((total + 15) >> 4);
+          for (uint32_t u = lane; u < units; u += 32) {
+            const uint32_t lo = u << 4, hi = lo + 16;
+            if (lo >= a && hi <= total) {
+              *reinterpret_cast<uint4 *>(gb + lo) = *reinterpret_cast<const uint4 *>(W.sout + lo);
+            } else {
+              for (uint32_t i = max(lo, a); i < min(hi, (uint32_t)total); i++) gb[i] = W.sout[i];
+            }
+          }
+          __syncwarp();
+        } else if (is_str && so + 5 + n <= str_cap) {
+          put_string(strs + so, (uint32_t)n, walk, sv.ptr(p0, src_end) , sv.ptr(p0, src_end) + (nxt - p0));
+        }
+      }
+      if (!valid) continue;
+
+      // ---- tape words ----------------------------------------------------------
       // Content is checked even where the grammar failed: a grammar code is
       // smaller than any content code, so the minimum keeps the grammar first.
       if (is_close(k)) {
@@ -388,46 +511,34 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         }
       } else if (is_atom(k)) {
         const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
-        const uint32_t n = k == K_FALSE ? 5 : 4;
-        bool ok = c.pos + n <= len;
-        for (uint32_t i = 0; ok && i < n; i++) ok = sv.at(c.pos + i) == (uint8_t)word[i];
-        if (ok && c.pos + n < len) ok = is_terminator(sv.at(c.pos + n));
+        const uint32_t nw = k == K_FALSE ? 5 : 4;
+        bool ok = pos + nw <= len;
+        for (uint32_t i = 0; ok && i < nw; i++) ok = sv.at(pos + i) == (uint8_t)word[i];
+        if (ok && pos + nw < len) ok = is_terminator(sv.at(pos + nw));
         if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
         else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
       } else if (k == K_NUMBER) {  // Sec. 3.2.1
         uint8_t tag;
         uint64_t v;
         int nc;
-        const uint64_t p0 = c.pos, p1 = c.next;
-        if (p1 < sv.slimit || (p1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
-          const uint8_t *sp = sv.smem + (p0 - sv.sbase);
-          nc = parse_number(sp, sp + (min(len, sv.slimit) - p0), tag, v);
+        const uint64_t q0 = pos, q1 = nxt;
+        if (q1 < sv.slimit || (q1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
+          const uint8_t *sp = sv.smem + (q0 - sv.sbase);
+          nc = parse_number(sp, sp + (min(len, sv.slimit) - q0), tag, v);
         } else {
-          nc = parse_number(doc + p0, doc + len, tag, v);
+          nc = parse_number(doc + q0, doc + len, tag, v);
         }
         if (nc) { if (!code) code = nc; }
         else if (tp + 1 < tape_cap) {
           tape[tp] = (uint64_t)tag << 56;
           tape[tp + 1] = v;
         }
-      } else if (k == K_STRING) {  // Sec. 3.2.2
-        if (sl & 0x80000000u) {
-          if (!code) code = (int)(sl & 0xFF);
-        } else if (tp < tape_cap && so + 5 + sl <= str_cap) {
-          tape[tp] = ((uint64_t)'"' << 56) | so;
-          uint8_t *o = strs + so;
-          o[0] = (uint8_t)sl; o[1] = (uint8_t)(sl >> 8); o[2] = (uint8_t)(sl >> 16); o[3] = (uint8_t)(sl >> 24);
-          int err;
-          const uint64_t p0 = (uint64_t)c.pos + 1, p1 = c.next;
-          const uint8_t *sp = sv.ptr(p0, p1);
-          string_walk<true>(sp, sp + (p1 - p0), err, o + 4);
-          o[4 + sl] = 0;
-        }
+      } else if (is_str && tp < tape_cap) {
+        tape[tp] = ((uint64_t)'"' << 56) | so;
       }
       if (code) report(J, d, g, code);
     }
-    __syncwarp();
-    tw.clear(W, lane);
+    __syncwarp();  // every lane is done with this tile's staged bytes
   }
 }
 

@@ -14,6 +14,7 @@ constexpr int kTileBytes = 32 * kBlockBytes;  // 2048
 constexpr int kS1Warps = 4;                   // tiles (warps) per stage-1 thread block
 constexpr int kS2Threads = 128;               // threads per stage-2 thread block
 constexpr int kMaxTileTokens = kTileBytes;    // at most one index per byte
+constexpr int kOpenGlobal = 2 * kMaxTileTokens + 1;  // relative levels [-2048, 2048] of one tile
 constexpr uint32_t kMaxDepthLimit = 4096;
 constexpr uint64_t kMaxDocBytes = 0xFFFFFF00ull;  // keeps positions and tape indices in u32
 constexpr uint32_t kSpinLimit = 1u << 24;         // bounded waits (polls) in look-back loops
@@ -79,7 +80,10 @@ struct Job {
   void *scan_pre;           // per scan block
   int32_t *spt;             // sparse table of tile `low` minima: level k at spt + k * spt_stride
   uint32_t spt_stride, spt_levels;
+  ulonglong2 *s1_qx;        // per 64-byte block: real quotes, backslash|control bytes
   uint32_t *slen;           // per index slot: normalised length of the string token there
+  uint64_t *meta;           // per index slot: token facts from the stage-2 reduce pass
+  uint16_t *open_g;         // per stage-2 reduce warp: level table for tiles with many tokens
   uint64_t *front;          // per index slot + tile: open container of each level entering a tile
   // outputs
   uint32_t *idx;
