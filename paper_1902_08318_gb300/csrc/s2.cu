@@ -34,8 +34,9 @@ constexpr int kHalo = 1024;                    // staged bytes past the tile's e
 constexpr int kStageBytes = kTileBytes + kHalo;
 constexpr int kStageBlocks = kStageBytes / kBlockBytes;
 constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
-constexpr int kOpenSmem = 1024;                // levels kept in shared memory (mod 1024)
-constexpr int kStrStage = 3328;                // string output of one chunk, staged
+constexpr int kOpenSmem = 512;                 // levels kept in shared memory (mod 512)
+constexpr int kStrStage = 3328;                // string output of 32 strings, staged
+constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
 
 // A string's entry in `slen`: an error code, or its normalised length and
 // whether it holds escapes (then the build pass walks it again).
@@ -43,20 +44,27 @@ constexpr uint32_t kSlenErr = 0x80000000u, kSlenWalk = 0x40000000u, kSlenLen = 0
 
 // Token facts passed from the reduce pass to the build pass, one word per
 // token: kind (4 bits), depth before the token relative to the tile (13 bits,
-// biased by 4096), tape slot relative to the tile (13), the enclosing
+// biased by 4096), tape slot relative to the tile (13), and the enclosing
 // container when it was opened in the tile (16: bit 15 valid, bit 14 object,
-// bits 0-11 its tape slot), and the string-buffer offset relative to the
-// tile (18).
+// bits 0-11 its tape slot).
 __device__ __forceinline__ uint64_t pack_meta(uint32_t kind, int32_t E, uint32_t tape,
-                                              uint32_t parent, uint32_t srel) {
+                                              uint32_t parent) {
   return (uint64_t)kind | ((uint64_t)(uint32_t)(E + 4096) << 4) | ((uint64_t)tape << 17) |
-         ((uint64_t)parent << 30) | ((uint64_t)srel << 46);
+         ((uint64_t)parent << 30);
 }
 
 __device__ __forceinline__ uint32_t warp_incl_u32(uint32_t v, int lane) {
 #pragma unroll
   for (int o = 1; o < 32; o <<= 1) {
     const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v += u;
+  }
+  return v;
+}
+__device__ __forceinline__ uint64_t warp_incl_u64(uint64_t v, int lane) {
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
     if (lane >= o) v += u;
   }
   return v;
@@ -122,6 +130,22 @@ struct Positions {
   }
 };
 
+// Work queues.  Per-token work whose cost depends on the token (string
+// lengths, numbers, string output) would leave most lanes of a chunk idle;
+// instead the tokens are queued in order and taken 32 at a time.
+struct QEntry {
+  uint32_t pos, nxt, j, tp;  // position, next token's position, index and tape slot in the tile
+};
+struct RQEntry {
+  uint32_t pos, nxt, j;
+};
+template <class T>
+__device__ __forceinline__ void enqueue(T *q, uint32_t &tail, bool take, const T &e, int lane) {
+  const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
+  if (take) q[(tail + __popc(m & ((1u << lane) - 1u))) & (kQueue - 1)] = e;
+  tail += __popc(m);
+}
+
 // ---------------------------------------------------------------------------
 // Stage-2 reduce: per tile, the depth change and lowest depth, tape words,
 // string-buffer bytes, and the containers left open at each level (the
@@ -132,6 +156,8 @@ struct __align__(16) ReduceSmem {  // 16-byte aligned size: bytes[] takes uint4 
   uint8_t bytes[kStageBytes + 64];
   uint64_t q[kStageBlocks];        // real quotes of the staged blocks
   uint64_t x[kStageBlocks];        // backslash and control bytes of the staged blocks
+  RQEntry sq[kQueue];              // strings awaiting their length
+  RQEntry wq[kQueue];              // strings with escapes awaiting a walk
   uint16_t open[kOpenSmem];
 };
 static_assert(sizeof(ReduceSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
@@ -139,8 +165,8 @@ static_assert(sizeof(ReduceSmem) % 16 == 0, "per-warp staging must stay 16-byte 
 // `open` entry of relative level l: the container currently open there, written
 // by the openers of the tile (0 = none, else bit 15, bit 14 = object, bits
 // 0-11 = the opener's tape slot relative to the tile).  A tile with fewer than
-// 1024 tokens spans fewer than 1024 levels, so they fit in shared memory
-// modulo 1024; other tiles use the warp's table in global memory.
+// 512 tokens spans fewer than 512 levels, so they fit in shared memory modulo
+// 512; other tiles use the warp's table in global memory.
 struct OpenTable {
   uint16_t *p;
   uint32_t mask;
@@ -184,7 +210,6 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
   uint16_t *const open_g = J.open_g + (uint64_t)(blockIdx.x * kS2Warps + wid) * kOpenGlobal;
   const uint32_t n_tiles = J.counters[2];
   const uint32_t warps = gridDim.x * kS2Warps;
-  const unsigned below = (1u << lane) - 1u;
   for (uint32_t t = blockIdx.x * kS2Warps + wid; t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
@@ -200,6 +225,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const uint64_t ib = idx_base(J, d);
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
+    uint32_t *slen = J.slen + ib + off;
     const uint64_t t0 = (uint64_t)tt * kTileBytes;
     // masks of the tile's blocks and of the next ones in the document
     const uint32_t nblk = min((uint32_t)kStageBlocks, (ntiles_d - tt) * 32u);
@@ -211,11 +237,50 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const Staged sv = stage_tile(W.bytes, doc, len, t0, lane);
     const OpenTable ot = cnt < (uint32_t)kOpenSmem ? OpenTable{W.open, (uint32_t)kOpenSmem - 1u, 0}
                                                    : OpenTable{open_g, 0xFFFFFFFFu, kLevelOff};
+    uint64_t sb = 0;  // string-buffer bytes of this lane's strings
+    uint32_t shead = 0, stail = 0, whead = 0, wtail = 0;
+    // strings: the next 32 queued get their length from the masks; those the
+    // masks cannot decide go to the walk queue
+    auto flush_strings = [&]() {
+      const uint32_t m = min(32u, stail - shead);
+      const bool have = (uint32_t)lane < m;
+      RQEntry e{0, 0, 0};
+      if (have) e = W.sq[(shead + lane) & (kQueue - 1)];
+      uint32_t L = 0;
+      const bool ok = have && plain_string_len(W, t0, (uint64_t)e.pos + 1, nblk, L);
+      if (ok) {
+        slen[e.j] = L;
+        sb += 5u + L;
+      }
+      enqueue(W.wq, wtail, have && !ok, e, lane);
+      shead += m;
+      __syncwarp();
+    };
+    // strings with escapes: walk them (Sec. 3.2.2), 32 at a time
+    auto flush_walks = [&]() {
+      const uint32_t m = min(32u, wtail - whead);
+      if ((uint32_t)lane < m) {
+        const RQEntry e = W.wq[(whead + lane) & (kQueue - 1)];
+        const uint64_t p0 = (uint64_t)e.pos + 1, p1 = e.nxt;
+        const uint8_t *sp = sv.ptr(p0, p1);
+        int err;
+        const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
+        if (err) {
+          slen[e.j] = kSlenErr | (uint32_t)err;
+          sb += 5u;
+        } else {
+          slen[e.j] = kSlenWalk | min(n, kSlenLen);
+          sb += 5ull + n;
+        }
+      }
+      whead += m;
+      __syncwarp();
+    };
+
     Positions ps;
     ps.begin(idxp, off, cnt, lane);
     int32_t depth = 0, mn = 0, mx = 0;
-    uint32_t tape = 0, srun = 0;
-    uint64_t sb = 0;
+    uint32_t tape = 0;
     for (uint32_t base = 0; base < cnt; base += 32) {
       const uint32_t j = base + lane;
       const bool valid = j < cnt;
@@ -229,65 +294,54 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
       const int32_t D = depth + (int32_t)(vi & 0xFFu) - (lane + 1);
       const int32_t E = D - dl;
       const uint32_t tp = tape + (vi >> 8) - w;
-      // enclosing container: the last opener of this chunk at the token's
-      // level, else the level table
+      // Enclosing container: depth moves by at most one per token, so it is
+      // the last earlier token whose depth-before is smaller (an opener at
+      // E - 1).  Found by a descent over window minima of E; when no token of
+      // this chunk qualifies, the level table holds it.
       const bool op = valid && is_open(kind);
       const uint16_t my = op ? (uint16_t)(0x8000u | (kind == K_OPEN_OBJ ? 0x4000u : 0u) | tp) : 0;
-      uint16_t parent = 0;
-      unsigned pending = __ballot_sync(0xFFFFFFFFu, valid);
-      while (pending) {
-        const int32_t lv = __shfl_sync(0xFFFFFFFFu, E, __ffs(pending) - 1);
-        const unsigned opl = __ballot_sync(0xFFFFFFFFu, op && D == lv);
-        const bool mine = ((pending >> lane) & 1u) && E == lv;
-        const unsigned m = opl & below;
-        const int src = (mine && m) ? 31 - __clz(m) : lane;
-        const uint16_t got = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, src);
-        if (mine) {
-          if (m) parent = got;
-          else if (lv > -kLevelOff && lv <= kLevelOff) parent = ot.at(lv);
-        }
-        pending &= ~__ballot_sync(0xFFFFFFFFu, mine);
-      }
+      int32_t m1 = valid ? E : 0x7FFFFFFF, m2, m4, m8, m16, u;
+      u = __shfl_up_sync(0xFFFFFFFFu, m1, 1);  m2 = lane >= 1 ? min(m1, u) : m1;
+      u = __shfl_up_sync(0xFFFFFFFFu, m2, 2);  m4 = lane >= 2 ? min(m2, u) : m2;
+      u = __shfl_up_sync(0xFFFFFFFFu, m4, 4);  m8 = lane >= 4 ? min(m4, u) : m4;
+      u = __shfl_up_sync(0xFFFFFFFFu, m8, 8);  m16 = lane >= 8 ? min(m8, u) : m8;
+      // mK at lane i: minimum of E over [i - K + 1, i] (clipped at lane 0)
+      int32_t at = lane - 1;
+      u = __shfl_sync(0xFFFFFFFFu, m16, max(at, 0));
+      if (at >= 0 && u >= E) at -= 16;
+      u = __shfl_sync(0xFFFFFFFFu, m8, max(at, 0));
+      if (at >= 0 && u >= E) at -= 8;
+      u = __shfl_sync(0xFFFFFFFFu, m4, max(at, 0));
+      if (at >= 0 && u >= E) at -= 4;
+      u = __shfl_sync(0xFFFFFFFFu, m2, max(at, 0));
+      if (at >= 0 && u >= E) at -= 2;
+      u = __shfl_sync(0xFFFFFFFFu, m1, max(at, 0));
+      if (at >= 0 && u >= E) at -= 1;
+      uint16_t parent = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, max(at, 0));
+      if (at < 0) parent = (valid && E > -kLevelOff && E <= kLevelOff) ? ot.at(E) : (uint16_t)0;
       // the last opener of each level of this chunk stays open for later tokens
       const unsigned grp = __match_any_sync(0xFFFFFFFFu, op ? D : 0x7FFFFFFF);
       if (op && lane == 31 - __clz(grp)) ot.at(D) = my;
-      // strings: normalised length (Sec. 3.2.2)
-      uint32_t enc = 0, ssz = 0;
-      if (valid && kind == K_STRING) {
-        const uint64_t p0 = (uint64_t)pos + 1;
-        uint32_t L;
-        if (plain_string_len(W, t0, p0, nblk, L)) {
-          enc = L;
-          ssz = 5u + L;
-        } else {
-          int err;
-          const uint64_t p1 = nxt;
-          const uint8_t *sp = sv.ptr(p0, p1);
-          const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
-          if (err) {
-            enc = kSlenErr | (uint32_t)err;
-            ssz = 5u;
-          } else {
-            enc = kSlenWalk | min(n, kSlenLen);
-            ssz = 5u + n;
-          }
-        }
-        sb += ssz;
-      }
-      const uint32_t si = warp_incl_u32(ssz, lane);
-      const uint32_t srel = srun + si - ssz;
       if (valid) {
-        J.meta[ib + off + j] = pack_meta(kind, E, tp, parent, srel);
-        if (kind == K_STRING) J.slen[ib + off + j] = enc;
+        J.meta[ib + off + j] = pack_meta(kind, E, tp, parent);
         mn = min(mn, min(E, D));
         mx = max(mx, max(E, D));
       }
+      enqueue(W.sq, stail, valid && kind == K_STRING, RQEntry{pos, nxt, j}, lane);
       const uint32_t tot = __shfl_sync(0xFFFFFFFFu, vi, 31);
       depth += (int32_t)(tot & 0xFFu) - 32;
       tape += tot >> 8;
-      srun += __shfl_sync(0xFFFFFFFFu, si, 31);
       __syncwarp();
+      if (stail - shead >= 32) {
+        flush_strings();
+        if (wtail - whead >= 32) flush_walks();
+      }
     }
+    while (shead != stail) {
+      flush_strings();
+      if (wtail - whead >= 32) flush_walks();
+    }
+    while (whead != wtail) flush_walks();
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
@@ -312,7 +366,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
 // ---------------------------------------------------------------------------
 struct __align__(16) BuildSmem {
   uint8_t bytes[kStageBytes + 64];
-  uint8_t sout[kStrStage];  // the string-buffer bytes of one chunk, before a coalesced copy
+  uint8_t sout[kStrStage];  // the string-buffer bytes of 32 strings, before a coalesced copy
+  QEntry nq[kQueue];        // numbers awaiting conversion
+  QEntry sq[kQueue];        // strings awaiting output
 };
 static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
               "per-warp staging must stay 16-byte aligned");
@@ -396,6 +452,94 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     }
 
     const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
+    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0;
+    uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
+
+    // numbers (Sec. 3.2.1), 32 at a time
+    auto flush_numbers = [&]() {
+      const uint32_t m = min(32u, ntail - nhead);
+      if ((uint32_t)lane < m) {
+        const QEntry e = W.nq[(nhead + lane) & (kQueue - 1)];
+        uint8_t tag;
+        uint64_t v;
+        int nc;
+        const uint64_t q0 = e.pos, q1 = e.nxt;
+        if (q1 < sv.slimit || (q1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
+          const uint8_t *sp = sv.smem + (q0 - sv.sbase);
+          nc = parse_number(sp, sp + (min(len, sv.slimit) - q0), tag, v);
+        } else {
+          nc = parse_number(doc + q0, doc + len, tag, v);
+        }
+        const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
+        if (nc) {
+          report(J, d, (uint64_t)off + e.j, nc);
+        } else if (tp + 1 < tape_cap) {
+          tape[tp] = (uint64_t)tag << 56;
+          tape[tp + 1] = v;
+        }
+      }
+      nhead += m;
+      __syncwarp();
+    };
+
+    // strings (Sec. 3.2.2), 32 at a time: their entries are contiguous in the
+    // buffer, so they are built in shared memory and copied out coalesced
+    auto flush_strings = [&]() {
+      const uint32_t m = min(32u, stail - shead);
+      const bool have = (uint32_t)lane < m;
+      QEntry e{0, 0, 0, 0};
+      if (have) e = W.sq[(shead + lane) & (kQueue - 1)];
+      const uint32_t sl = have ? J.slen[ib + off + e.j] : 0u;
+      const bool bad = have && (sl & kSlenErr);
+      if (bad) report(J, d, (uint64_t)off + e.j, (int)(sl & 0xFFu));
+      const bool is_str = have && !bad;
+      const bool walk = (sl & kSlenWalk) != 0;
+      const uint64_t p0 = (uint64_t)e.pos + 1;
+      uint64_t n = sl & kSlenLen;
+      if (is_str && n == kSlenLen) {  // too long for the entry: measure again
+        int err;
+        n = string_walk<false>(doc + p0, doc + e.nxt, err, nullptr);
+      }
+      const uint64_t size = have ? (bad ? 5ull : 5ull + n) : 0ull;
+      const uint64_t incl = warp_incl_u64(size, lane);
+      const uint64_t so = str_run + incl - size;
+      const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
+      if (is_str && tp < tape_cap) tape[tp] = ((uint64_t)'"' << 56) | so;
+      const uint64_t src_end = walk ? (uint64_t)e.nxt : p0 + n;
+      const bool fits = !is_str || (n < kSlenLen && src_end <= sv.slimit);
+      const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
+      if (sm) {
+        const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
+        const uint64_t so_lo = __shfl_sync(0xFFFFFFFFu, so, __ffs(sm) - 1);
+        const uint64_t so_hi = __shfl_sync(0xFFFFFFFFu, so + 5 + n, 31 - __clz(sm));
+        const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
+        const uint64_t total = a + (so_hi - so_lo);
+        if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
+          if (is_str) {
+            const uint8_t *sp = sv.smem + (p0 - sv.sbase);
+            put_string(W.sout + a + (so - so_lo), (uint32_t)n, walk, sp, sp + (e.nxt - p0));
+          }
+          __syncwarp();
+          uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
+          const uint32_t units = (uint32_t)((total + 15) >> 4);
+          for (uint32_t u = lane; u < units; u += 32) {
+            const uint32_t lo = u << 4, hi = lo + 16;
+            if (lo >= a && hi <= total) {
+              *reinterpret_cast<uint4 *>(gb + lo) = *reinterpret_cast<const uint4 *>(W.sout + lo);
+            } else {
+              for (uint32_t i = max(lo, a); i < min(hi, (uint32_t)total); i++) gb[i] = W.sout[i];
+            }
+          }
+        } else if (is_str && so + 5 + n <= str_cap) {
+          const uint8_t *sp = sv.ptr(p0, src_end);
+          put_string(strs + so, (uint32_t)n, walk, sp, sp + (e.nxt - p0));
+        }
+      }
+      str_run += __shfl_sync(0xFFFFFFFFu, incl, 31);
+      shead += m;
+      __syncwarp();
+    };
+
     Positions ps;
     ps.begin(idxp, off, cnt, lane);
     // kinds of the two tokens before the tile
@@ -414,9 +558,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       const uint64_t meta = valid ? J.meta[ib + off + j] : 0ull;
       const uint8_t k = (uint8_t)(meta & 15u);
       const int32_t E = pre.d_start + ((int32_t)((meta >> 4) & 0x1FFFu) - 4096);
-      const uint64_t tp = (uint64_t)pre.tape_start + ((meta >> 17) & 0x1FFFu);
+      const uint32_t trel = (uint32_t)(meta >> 17) & 0x1FFFu;
+      const uint64_t tp = (uint64_t)pre.tape_start + trel;
       const uint32_t parent = (uint32_t)(meta >> 30) & 0xFFFFu;
-      const uint64_t so = pre.str_start + (meta >> 46);
       uint8_t p = __shfl_up_sync(0xFFFFFFFFu, k, 1);
       uint8_t pp = __shfl_up_sync(0xFFFFFFFFu, k, 2);
       if (lane == 0) { p = prev1; pp = prev2; }
@@ -457,87 +601,34 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       }
       if (!code && is_open(k) && E + 1 > (int32_t)max_depth) code = SJ_DEPTH_ERROR;
 
-      // ---- strings (Sec. 3.2.2): one chunk's entries are contiguous in the
-      //      buffer; stage them in shared memory and copy them out coalesced ----
-      const uint32_t sl = (valid && k == K_STRING) ? J.slen[ib + off + j] : 0u;
-      const bool is_str = valid && k == K_STRING && !(sl & kSlenErr);
-      if (valid && k == K_STRING && (sl & kSlenErr) && !code) code = (int)(sl & 0xFFu);
-      const bool walk = (sl & kSlenWalk) != 0;
-      const uint64_t p0 = (uint64_t)pos + 1;
-      uint64_t n = sl & kSlenLen;
-      if (is_str && n == kSlenLen) {  // too long for the entry: measure again
-        int err;
-        n = string_walk<false>(doc + p0, doc + nxt, err, nullptr);
-      }
-      const uint64_t src_end = walk ? (uint64_t)nxt : p0 + n;
-      const bool fits = !is_str || (n < kSlenLen && src_end <= sv.slimit);
-      const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
-      if (sm) {
-        const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
-        const uint64_t so_lo = __shfl_sync(0xFFFFFFFFu, so, __ffs(sm) - 1);
-        const uint64_t so_hi = __shfl_sync(0xFFFFFFFFu, so + 5 + n, 31 - __clz(sm));
-        const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
-        const uint64_t total = a + (so_hi - so_lo);
-        if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (is_str) {
-            const uint8_t *sp = sv.smem + (p0 - sv.sbase);
-            put_string(W.sout + a + (so - so_lo), (uint32_t)n, walk, sp, sp + (nxt - p0));
-          }
-          __syncwarp();
-          uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
-          const uint32_t units = (uint32_t)((total + 15) >> 4);
-          for (uint32_t u = lane; u < units; u += 32) {
-            const uint32_t lo = u << 4, hi = lo + 16;
-            if (lo >= a && hi <= total) {
-              *reinterpret_cast<uint4 *>(gb + lo) = *reinterpret_cast<const uint4 *>(W.sout + lo);
-            } else {
-              for (uint32_t i = max(lo, a); i < min(hi, (uint32_t)total); i++) gb[i] = W.sout[i];
-            }
-          }
-          __syncwarp();
-        } else if (is_str && so + 5 + n <= str_cap) {
-          put_string(strs + so, (uint32_t)n, walk, sv.ptr(p0, src_end) , sv.ptr(p0, src_end) + (nxt - p0));
-        }
-      }
-      if (!valid) continue;
-
-      // ---- tape words ----------------------------------------------------------
+      // ---- tape words of closers and atoms; numbers and strings are queued.
       // Content is checked even where the grammar failed: a grammar code is
       // smaller than any content code, so the minimum keeps the grammar first.
-      if (is_close(k)) {
-        if (!code && tp < tape_cap && par_tape < tape_cap) {
-          tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
-          tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
+      if (valid) {
+        if (is_close(k)) {
+          if (!code && tp < tape_cap && par_tape < tape_cap) {
+            tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
+            tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
+          }
+        } else if (is_atom(k)) {
+          const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
+          const uint32_t nw = k == K_FALSE ? 5 : 4;
+          bool ok = pos + nw <= len;
+          for (uint32_t i = 0; ok && i < nw; i++) ok = sv.at(pos + i) == (uint8_t)word[i];
+          if (ok && pos + nw < len) ok = is_terminator(sv.at(pos + nw));
+          if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
+          else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
         }
-      } else if (is_atom(k)) {
-        const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
-        const uint32_t nw = k == K_FALSE ? 5 : 4;
-        bool ok = pos + nw <= len;
-        for (uint32_t i = 0; ok && i < nw; i++) ok = sv.at(pos + i) == (uint8_t)word[i];
-        if (ok && pos + nw < len) ok = is_terminator(sv.at(pos + nw));
-        if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
-        else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
-      } else if (k == K_NUMBER) {  // Sec. 3.2.1
-        uint8_t tag;
-        uint64_t v;
-        int nc;
-        const uint64_t q0 = pos, q1 = nxt;
-        if (q1 < sv.slimit || (q1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
-          const uint8_t *sp = sv.smem + (q0 - sv.sbase);
-          nc = parse_number(sp, sp + (min(len, sv.slimit) - q0), tag, v);
-        } else {
-          nc = parse_number(doc + q0, doc + len, tag, v);
-        }
-        if (nc) { if (!code) code = nc; }
-        else if (tp + 1 < tape_cap) {
-          tape[tp] = (uint64_t)tag << 56;
-          tape[tp + 1] = v;
-        }
-      } else if (is_str && tp < tape_cap) {
-        tape[tp] = ((uint64_t)'"' << 56) | so;
+        if (code) report(J, d, g, code);
       }
-      if (code) report(J, d, g, code);
+      enqueue(W.nq, ntail, valid && k == K_NUMBER, QEntry{pos, nxt, j, trel}, lane);
+      enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel}, lane);
+      __syncwarp();
+      if (ntail - nhead >= 32) flush_numbers();
+      if (stail - shead >= 32) flush_strings();
     }
+    while (nhead != ntail) flush_numbers();
+    while (shead != stail) flush_strings();
     __syncwarp();  // every lane is done with this tile's staged bytes
   }
 }
