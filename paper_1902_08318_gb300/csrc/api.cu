@@ -57,6 +57,7 @@ struct sj_parser {
   ulonglong2 *d_s1_qx = nullptr;
   uint64_t *d_meta = nullptr;
   uint16_t *d_open_g = nullptr;
+  uint8_t *d_unesc = nullptr;
   uint64_t *d_front = nullptr;
   uint32_t *d_surv = nullptr;
   uint32_t *d_idx = nullptr;
@@ -119,7 +120,7 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
                  p->d_scan_agg, p->d_scan_pre, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
                  p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
-                 p->d_open_g};
+                 p->d_open_g, p->d_unesc};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_job) cudaFreeHost(p->h_job);
@@ -156,6 +157,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(&p->d_slen, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(&p->d_meta, max_bytes + 16))) return r;
+  if ((r = dalloc(&p->d_unesc, max_bytes + 64))) return r;
   if ((r = dalloc(&p->d_front, max_bytes + tiles + 16))) return r;
   if ((r = dalloc(&p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(&p->d_idx, max_bytes + 16))) return r;
@@ -217,6 +219,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.s1_qx = p->d_s1_qx;
   J.meta = p->d_meta;
   J.open_g = p->d_open_g;
+  J.unesc = p->d_unesc;
   J.front = p->d_front;
   J.surv = p->d_surv;
   J.idx = p->d_idx;

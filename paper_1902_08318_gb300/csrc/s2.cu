@@ -39,7 +39,8 @@ constexpr int kStrStage = 3328;                // string output of 32 strings, s
 constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
 
 // A string's entry in `slen`: an error code, or its normalised length and
-// whether it holds escapes (then the build pass walks it again).
+// whether it holds escapes (then the reduce pass has left its normalised bytes
+// in the scratch buffer `unesc`, at the string's own position).
 constexpr uint32_t kSlenErr = 0x80000000u, kSlenWalk = 0x40000000u, kSlenLen = 0x3FFFFFFFu;
 
 // Token facts passed from the reduce pass to the build pass, one word per
@@ -139,6 +140,7 @@ struct QEntry {
 struct RQEntry {
   uint32_t pos, nxt, j;
 };
+
 template <class T>
 __device__ __forceinline__ void enqueue(T *q, uint32_t &tail, bool take, const T &e, int lane) {
   const unsigned m = __ballot_sync(0xFFFFFFFFu, take);
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
     uint32_t *slen = J.slen + ib + off;
+    uint8_t *unesc = J.unesc + rel_off(J, d);
     const uint64_t t0 = (uint64_t)tt * kTileBytes;
     // masks of the tile's blocks and of the next ones in the document
     const uint32_t nblk = min((uint32_t)kStageBlocks, (ntiles_d - tt) * 32u);
@@ -264,7 +267,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
         const uint64_t p0 = (uint64_t)e.pos + 1, p1 = e.nxt;
         const uint8_t *sp = sv.ptr(p0, p1);
         int err;
-        const uint32_t n = string_walk<false>(sp, sp + (p1 - p0), err, nullptr);
+        // normalised bytes are never more than the raw ones: they stay within
+        // the string's own span of the scratch buffer
+        const uint32_t n = string_walk<true>(sp, sp + (p1 - p0), err, unesc + p0);
         if (err) {
           slen[e.j] = kSlenErr | (uint32_t)err;
           sb += 5u;
@@ -395,16 +400,13 @@ __device__ __forceinline__ uint16_t grammar_row(uint32_t k, bool obj) {
   }
 }
 
-// Write one string's buffer entry (u32 length, bytes, NUL) at o.
-__device__ __forceinline__ void put_string(uint8_t *o, uint32_t n, bool walk, const uint8_t *sp,
-                                           const uint8_t *lim) {
+// Write one string's buffer entry (u32 length, its n normalised bytes from
+// src, NUL) at o.
+__device__ __forceinline__ void put_string(uint8_t *__restrict__ o, uint32_t n,
+                                           const uint8_t *__restrict__ src) {
   o[0] = (uint8_t)n; o[1] = (uint8_t)(n >> 8); o[2] = (uint8_t)(n >> 16); o[3] = (uint8_t)(n >> 24);
-  if (walk) {
-    int err;
-    string_walk<true>(sp, lim, err, o + 4);
-  } else {
-    for (uint32_t i = 0; i < n; i++) o[4 + i] = sp[i];
-  }
+#pragma unroll 4
+  for (uint32_t i = 0; i < n; i++) o[4 + i] = src[i];
   o[4 + n] = 0;
 }
 
@@ -453,6 +455,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
 
     const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
     uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0;
+    const uint8_t *unesc = J.unesc + rel_off(J, d);
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
     // numbers (Sec. 3.2.1), 32 at a time
@@ -505,8 +508,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       const uint64_t so = str_run + incl - size;
       const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
       if (is_str && tp < tape_cap) tape[tp] = ((uint64_t)'"' << 56) | so;
-      const uint64_t src_end = walk ? (uint64_t)e.nxt : p0 + n;
-      const bool fits = !is_str || (n < kSlenLen && src_end <= sv.slimit);
+      // the bytes come from the staged input, or for strings with escapes from
+      // the normalised copy the reduce pass left in the scratch buffer
+      const bool fits = !is_str || walk || p0 + n <= sv.slimit;
       const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
       if (sm) {
         const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
@@ -515,10 +519,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
         const uint64_t total = a + (so_hi - so_lo);
         if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (is_str) {
-            const uint8_t *sp = sv.smem + (p0 - sv.sbase);
-            put_string(W.sout + a + (so - so_lo), (uint32_t)n, walk, sp, sp + (e.nxt - p0));
-          }
+          if (is_str)
+            put_string(W.sout + a + (so - so_lo), (uint32_t)n,
+                       walk ? unesc + p0 : sv.smem + (p0 - sv.sbase));
           __syncwarp();
           uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
           const uint32_t units = (uint32_t)((total + 15) >> 4);
@@ -531,8 +534,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
             }
           }
         } else if (is_str && so + 5 + n <= str_cap) {
-          const uint8_t *sp = sv.ptr(p0, src_end);
-          put_string(strs + so, (uint32_t)n, walk, sp, sp + (e.nxt - p0));
+          put_string(strs + so, (uint32_t)n, walk ? unesc + p0 : sv.ptr(p0, p0 + n));
         }
       }
       str_run += __shfl_sync(0xFFFFFFFFu, incl, 31);

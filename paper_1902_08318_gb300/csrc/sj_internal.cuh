@@ -83,6 +83,7 @@ struct Job {
   ulonglong2 *s1_qx;        // per 64-byte block: real quotes, backslash|control bytes
   uint32_t *slen;           // per index slot: normalised length of the string token there
   uint64_t *meta;           // per index slot: token facts from the stage-2 reduce pass
+  uint8_t *unesc;           // per input byte: normalised strings with escapes, at their position
   uint16_t *open_g;         // per stage-2 reduce warp: level table for tiles with many tokens
   uint64_t *front;          // per index slot + tile: open container of each level entering a tile
   // outputs
