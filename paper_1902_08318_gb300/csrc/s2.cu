@@ -136,6 +136,11 @@ struct Positions {
 // instead the tokens are queued in order and taken 32 at a time.
 struct QEntry {
   uint32_t pos, nxt, j, tp;  // position, next token's position, index and tape slot in the tile
+  uint32_t sl;               // a string's `slen` entry
+};
+struct WQEntry {
+  uint64_t so;               // buffer offset of the string's entry
+  uint32_t p0, n;            // first content byte, normalised length
 };
 struct RQEntry {
   uint32_t pos, nxt, j;
@@ -374,6 +379,7 @@ struct __align__(16) BuildSmem {
   uint8_t sout[kStrStage];  // the string-buffer bytes of 32 strings, before a coalesced copy
   QEntry nq[kQueue];        // numbers awaiting conversion
   QEntry sq[kQueue];        // strings awaiting output
+  WQEntry wq[kQueue];       // strings with escapes awaiting output
 };
 static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
               "per-warp staging must stay 16-byte aligned");
@@ -454,7 +460,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     }
 
     const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
-    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0;
+    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0, whead = 0, wtail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
@@ -490,9 +496,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     auto flush_strings = [&]() {
       const uint32_t m = min(32u, stail - shead);
       const bool have = (uint32_t)lane < m;
-      QEntry e{0, 0, 0, 0};
+      QEntry e{0, 0, 0, 0, 0};
       if (have) e = W.sq[(shead + lane) & (kQueue - 1)];
-      const uint32_t sl = have ? J.slen[ib + off + e.j] : 0u;
+      const uint32_t sl = e.sl;
       const bool bad = have && (sl & kSlenErr);
       if (bad) report(J, d, (uint64_t)off + e.j, (int)(sl & 0xFFu));
       const bool is_str = have && !bad;
@@ -508,10 +514,14 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       const uint64_t so = str_run + incl - size;
       const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
       if (is_str && tp < tape_cap) tape[tp] = ((uint64_t)'"' << 56) | so;
-      // the bytes come from the staged input, or for strings with escapes from
-      // the normalised copy the reduce pass left in the scratch buffer
-      const bool fits = !is_str || walk || p0 + n <= sv.slimit;
-      const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
+      // Strings with escapes take their normalised bytes from the scratch buffer
+      // of the reduce pass, in flush_walks; the copy below leaves their bytes
+      // undefined until then.
+      enqueue(W.wq, wtail, is_str && walk,
+              WQEntry{so, (uint32_t)p0, (uint32_t)min(n, (uint64_t)0xFFFFFFFFu)}, lane);
+      const bool plain = is_str && !walk;
+      const bool fits = !plain || p0 + n <= sv.slimit;
+      const unsigned sm = __ballot_sync(0xFFFFFFFFu, plain);
       if (sm) {
         const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
         const uint64_t so_lo = __shfl_sync(0xFFFFFFFFu, so, __ffs(sm) - 1);
@@ -519,9 +529,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
         const uint64_t total = a + (so_hi - so_lo);
         if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (is_str)
-            put_string(W.sout + a + (so - so_lo), (uint32_t)n,
-                       walk ? unesc + p0 : sv.smem + (p0 - sv.sbase));
+          if (plain) put_string(W.sout + a + (so - so_lo), (uint32_t)n, sv.smem + (p0 - sv.sbase));
           __syncwarp();
           uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
           const uint32_t units = (uint32_t)((total + 15) >> 4);
@@ -533,8 +541,8 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
               for (uint32_t i = max(lo, a); i < min(hi, (uint32_t)total); i++) gb[i] = W.sout[i];
             }
           }
-        } else if (is_str && so + 5 + n <= str_cap) {
-          put_string(strs + so, (uint32_t)n, walk ? unesc + p0 : sv.ptr(p0, p0 + n));
+        } else if (plain && so + 5 + n <= str_cap) {
+          put_string(strs + so, (uint32_t)n, sv.ptr(p0, p0 + n));
         }
       }
       str_run += __shfl_sync(0xFFFFFFFFu, incl, 31);
@@ -542,8 +550,26 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       __syncwarp();
     };
 
+    // Strings with escapes, up to 32: the scratch bytes around the tile are
+    // staged in sout, then the warp copies one string at a time.
+    auto flush_walks = [&]() {
+      const uint32_t m = min(32u, wtail - whead);
+      const Staged us = stage_tile(W.sout, unesc, len, (uint64_t)tt * kTileBytes, lane);
+      for (uint32_t i = 0; i < m; i++) {
+        const WQEntry e = W.wq[(whead + i) & (kQueue - 1)];
+        if (e.so + 5 + e.n > str_cap) continue;
+        const uint8_t *src = us.ptr(e.p0, (uint64_t)e.p0 + e.n);
+        uint8_t *dst = strs + e.so;
+        for (uint32_t b = lane; b < e.n + 5; b += 32)
+          dst[b] = b < 4 ? (uint8_t)(e.n >> (8 * b)) : (b < e.n + 4 ? src[b - 4] : (uint8_t)0);
+      }
+      whead += m;
+      __syncwarp();
+    };
+
     Positions ps;
     ps.begin(idxp, off, cnt, lane);
+    uint64_t meta_next = (uint32_t)lane < cnt ? J.meta[ib + off + lane] : 0ull;
     // kinds of the two tokens before the tile
     uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
     if (lane < 2 && off >= (uint32_t)lane + 1) {
@@ -557,8 +583,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       const bool valid = j < cnt;
       uint32_t pos, nxt;
       ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
-      const uint64_t meta = valid ? J.meta[ib + off + j] : 0ull;
+      const uint64_t meta = meta_next;
+      meta_next = j + 32 < cnt ? J.meta[ib + off + j + 32] : 0ull;
       const uint8_t k = (uint8_t)(meta & 15u);
+      const uint32_t sl = (valid && k == K_STRING) ? J.slen[ib + off + j] : 0u;
       const int32_t E = pre.d_start + ((int32_t)((meta >> 4) & 0x1FFFu) - 4096);
       const uint32_t trel = (uint32_t)(meta >> 17) & 0x1FFFu;
       const uint64_t tp = (uint64_t)pre.tape_start + trel;
@@ -623,14 +651,21 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         }
         if (code) report(J, d, g, code);
       }
-      enqueue(W.nq, ntail, valid && k == K_NUMBER, QEntry{pos, nxt, j, trel}, lane);
-      enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel}, lane);
+      enqueue(W.nq, ntail, valid && k == K_NUMBER, QEntry{pos, nxt, j, trel, 0}, lane);
+      enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel, sl}, lane);
       __syncwarp();
       if (ntail - nhead >= 32) flush_numbers();
-      if (stail - shead >= 32) flush_strings();
+      if (stail - shead >= 32) {
+        flush_strings();
+        if (wtail - whead >= 32) flush_walks();
+      }
     }
     while (nhead != ntail) flush_numbers();
-    while (shead != stail) flush_strings();
+    while (shead != stail) {
+      flush_strings();
+      if (wtail - whead >= 32) flush_walks();
+    }
+    while (whead != wtail) flush_walks();
     __syncwarp();  // every lane is done with this tile's staged bytes
   }
 }
