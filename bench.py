@@ -16,6 +16,11 @@ header read back).  `roofline` reports the dominant kernel against the
 measured HBM copy bandwidth; `cpu_baseline` times the CPU oracle on a bounded
 sample of the same workload on this host's cores.
 
+Two more objects ride on the same line: `batch` (the 100,000-document batch
+of config3 in one graph-launched run, against the same documents parsed one
+per launch) and `serving` (the config4 arrival trace replayed against the
+continuous-batching server: docs/s, GB/s, p50/p99 latency).
+
 --impl reference times the CPU oracle itself (the only reference that exists
 for this workload) on a bounded sample per step.
 
@@ -307,6 +312,92 @@ def report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_s
     return out
 
 
+def pct(x, q) -> float:
+    return float(np.percentile(np.asarray(x), q))
+
+
+def batch_leg(args, dev) -> dict:
+    """Batched: the 100,000-document batch (config3) in one graph-launched run,
+    against the same documents parsed one per launch."""
+    import torch
+
+    import gen
+    import paper_1902_08318_gb300 as sj
+    buf, off = gen.config3()
+    n = off.size - 1
+    total = int(off[-1])
+    buf_dev = torch.from_numpy(np.require(buf, requirements=["W"])).to(dev)
+    p = sj.Parser(max_bytes=total + 64, max_docs=n)
+    res, _ = p.parse_batch(buf_dev, off)
+    for _ in range(args.warmup):
+        p.parse_batch(buf_dev, off)
+    torch.cuda.synchronize()
+    k = max(3, min(args.steps, 10))
+    lat = []
+    for _ in range(k):
+        t0 = time.perf_counter()
+        p.parse_batch(buf_dev, off)  # waits for the run and its result copy
+        lat.append(time.perf_counter() - t0)
+    dt = sum(lat)
+    # one document per launch (sj_parse), on the first documents of the batch
+    single = sj.Parser(max_bytes=(1 << 20) + 64)
+    m = min(n, 5000)
+    for i in range(50):
+        single.parse(buf_dev[int(off[i]): int(off[i + 1])])
+    torch.cuda.synchronize()
+    one = []
+    t_all = time.perf_counter()
+    for i in range(m):
+        t0 = time.perf_counter()
+        single.parse(buf_dev[int(off[i]): int(off[i + 1])])
+        one.append(time.perf_counter() - t0)
+    t_all = time.perf_counter() - t_all
+    return {
+        "workload": "config3: 100,000 documents of the config-0 generator, log-normal sizes "
+                    "(median 2 KB, sigma 1.5, 100 B - 1 MB), 1% with one defect",
+        "docs": n, "bytes": total, "invalid_docs": int(np.count_nonzero(res["error"])),
+        "batched": {"docs_per_s": round(n * k / dt, 1), "GB_per_s": round(total * k / dt / 1e9, 2),
+                    "ms_per_batch": round(dt / k * 1e3, 3),
+                    "latency_ms_p50": round(pct(lat, 50) * 1e3, 3),
+                    "latency_ms_p99": round(pct(lat, 99) * 1e3, 3),
+                    "launches_per_batch": p.kernels_per_run(), "steps": k},
+        "one_per_launch": {"docs": m, "docs_per_s": round(m / t_all, 1),
+                           "GB_per_s": round(int(off[m]) / t_all / 1e9, 3),
+                           "latency_ms_p50": round(pct(one, 50) * 1e3, 4),
+                           "latency_ms_p99": round(pct(one, 99) * 1e3, 4)},
+        "timing": "host clock around each synchronous call (batch: all 100,000 results ready)",
+    }
+
+
+def serving_leg(args) -> dict:
+    """Serving (config4): the arrival trace replayed natively against the
+    continuous-batching server (latency = result seen minus arrival)."""
+    import gen
+    import paper_1902_08318_gb300 as sj
+    arrival, buf, off = gen.config4(workers=max(1, min(16, os.cpu_count() or 1)))
+    n = arrival.size
+    srv = sj.Server(max_batch_bytes=16 << 20, max_batch_docs=4096, max_slots=8,
+                    mem_budget=8 << 30)
+    # warm-up: a slice of the trace (captures the graphs of every batch size)
+    w = 20_000
+    srv.replay(buf, off[: w + 1], arrival[:w] - arrival[0])
+    b0 = srv.batches
+    lat, wall = srv.replay(buf, off, arrival)
+    batches = srv.batches - b0
+    return {
+        "workload": "config4: 200,000 requests, Poisson arrivals at 50,000/s, log-normal sizes "
+                    "(median 4 KB, sigma 2, 64 B - 8 MB), 60% records / 25% number-heavy / "
+                    "15% string-heavy",
+        "requests": int(n), "bytes": int(off[-1]), "offered_req_per_s": round(n / float(arrival[-1]), 1),
+        "docs_per_s": round(n / wall, 1), "GB_per_s": round(int(off[-1]) / wall / 1e9, 3),
+        "latency_ms_p50": round(pct(lat, 50) * 1e3, 4), "latency_ms_p99": round(pct(lat, 99) * 1e3, 4),
+        "latency_ms_max": round(float(lat.max()) * 1e3, 3),
+        "slots": srv.slots, "device_bytes": srv.device_bytes, "mem_budget": 8 << 30,
+        "batches": int(batches), "docs_per_batch": round(n / max(1, batches), 2),
+        "timing": "host clock; arrival = scheduled time, done = result seen by the polling loop",
+    }
+
+
 def oracle_gbs(sample: bytes, repeats: int = 1) -> tuple[float, float]:
     import oracle
     oracle.parse(sample[:1024])  # build + warm
@@ -378,6 +469,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS), default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
+    ap.add_argument("--no-batch", action="store_true", help="skip the batched (config3) leg")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving (config4) leg")
     ap.add_argument("--doc-mb", type=int, default=0,
                     help="config2 document size in MiB (default 1024; smaller for ncu captures)")
     args = ap.parse_args()
@@ -404,6 +497,12 @@ def main():
         dist.barrier()
     out = run_ours(args, rank, world, dist)
     if out is not None:
+        import torch
+        dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+        if not args.no_batch:
+            out["batch"] = batch_leg(args, dev)
+        if not args.no_serving:
+            out["serving"] = serving_leg(args)
         if not args.no_cpu_baseline:
             out["cpu_baseline"] = cpu_baseline(args)
         print(json.dumps(out), flush=True)

@@ -73,7 +73,7 @@ def _load():
 
 
 def _call(fn, target: int, *args, out: np.ndarray | None = None) -> np.ndarray:
-    slack = 1 << 20
+    slack = (16 << 10) + target // 8
     while True:
         cap = target + slack
         buf = out if (out is not None and out.size >= cap) else np.empty(cap, dtype=np.uint8)
@@ -168,25 +168,41 @@ def config3(seed: int = 3000, n_docs: int = 100_000, invalid_frac: float = 0.01)
     return np.frombuffer(b"".join(parts), dtype=np.uint8), offsets
 
 
+def _serving_docs(args) -> tuple[bytes, list[int]]:
+    """Documents [lo, hi) of a serving stream (worker of config4)."""
+    seed, lo, hi, sizes, mix = args
+    parts = []
+    for k, i in enumerate(range(lo, hi)):
+        s = seed * 1_000_003 + i
+        if mix[k] < 0.60:
+            doc = records(s, int(sizes[k]), root_array=False, pretty=True)
+        elif mix[k] < 0.85:
+            doc = geo(s, int(sizes[k]))
+        else:
+            doc = strings_heavy(s, int(sizes[k]))
+        parts.append(doc.tobytes())
+    return b"".join(parts), [len(p) for p in parts]
+
+
 def config4(seed: int = 4000, n_req: int = 200_000, rate: float = 50_000.0,
-            max_size: int = 8 << 20):
-    """Serving stream.  Returns (arrival_s float64[n], buf uint8, offsets uint64[n+1])."""
+            max_size: int = 8 << 20, workers: int = 1):
+    """Serving stream.  Returns (arrival_s float64[n], buf uint8, offsets uint64[n+1]).
+    workers > 1 generates in that many processes (same bytes)."""
     rng = np.random.Generator(np.random.PCG64(seed))
     gaps = rng.exponential(1.0 / rate, n_req)
     arrival = np.cumsum(gaps)
     sizes = _lognormal_sizes(rng, n_req, 4096, 2.0, 64, max_size)
     mix = rng.random(n_req)
-    parts = []
-    for i in range(n_req):
-        s = seed * 1_000_003 + i
-        if mix[i] < 0.60:
-            doc = records(s, int(sizes[i]), root_array=False, pretty=True)
-        elif mix[i] < 0.85:
-            doc = geo(s, int(sizes[i]))
-        else:
-            doc = strings_heavy(s, int(sizes[i]))
-        parts.append(doc.tobytes())
-    lens = np.array([len(p) for p in parts], dtype=np.uint64)
+    step = max(1, -(-n_req // (8 * max(1, workers))))
+    jobs = [(seed, lo, min(n_req, lo + step), sizes[lo: lo + step], mix[lo: lo + step])
+            for lo in range(0, n_req, step)]
+    if workers > 1:
+        import multiprocessing as mp
+        with mp.get_context("spawn").Pool(workers) as pool:
+            results = pool.map(_serving_docs, jobs)
+    else:
+        results = [_serving_docs(j) for j in jobs]
+    lens = np.array([n for _, ls in results for n in ls], dtype=np.uint64)
     offsets = np.zeros(n_req + 1, dtype=np.uint64)
     np.cumsum(lens, out=offsets[1:])
-    return arrival, np.frombuffer(b"".join(parts), dtype=np.uint8), offsets
+    return arrival, np.frombuffer(b"".join(b for b, _ in results), dtype=np.uint8), offsets

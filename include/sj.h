@@ -14,9 +14,9 @@
  *    result (valid or which error) is reported separately, in sj_result.error
  *    or sj_doc_result.error, as an sj_error code.
  *  - Input bytes may live in host or device memory (detected with
- *    cudaPointerGetAttributes).  They are read-only and need no padding.
- *    Host input, and device input that is not 16-byte aligned, is first copied
- *    into a parser-owned device buffer.
+ *    cudaPointerGetAttributes).  They are read-only and need neither padding
+ *    nor alignment.  Host input is first copied into a parser-owned device
+ *    buffer; device input is read in place.
  *  - Outputs live in parser-owned device buffers and stay valid until the next
  *    call on the same parser.  The caller never frees them.
  *  - A parser is not thread-safe; use one parser per host thread.
@@ -108,7 +108,8 @@ typedef struct {
 /* Create a parser for inputs of at most max_bytes bytes in total (summed over
  * a batch) and at most max_docs documents per batch (0 = 1).  max_depth is
  * the nesting limit (0 = 4096; at most 4096); the root container has depth 1.
- * Allocates all device memory up front (about 22 bytes per input byte).
+ * Allocates all device memory up front (about 45 bytes per input byte, plus
+ * about 40 MB of per-warp tables; sj_parser_device_bytes tells the total).
  * Returns SJ_SUCCESS and *out, or an error status and *out = NULL. */
 sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint32_t max_docs,
                            uint32_t max_depth);
@@ -136,6 +137,81 @@ sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc
                          uint32_t n_docs, void *stream, sj_doc_result *out,
                          const uint32_t **indices, const uint64_t **tape,
                          const uint8_t **strings);
+
+/* sj_parse_batch in two halves.  sj_parse_batch_async queues the run on
+ * `stream` and returns; host `bytes` should be pinned (cudaMallocHost) for the
+ * copy to be asynchronous, and must stay unchanged until the run has finished.
+ * sj_parse_query returns 1 when the queued run has finished (or none is
+ * queued), 0 while it runs, and -status on a CUDA error.  sj_parse_batch_wait
+ * waits for the run and fills the outputs as sj_parse_batch does. */
+sj_status sj_parse_batch_async(sj_parser *p, const uint8_t *bytes, const uint64_t *doc_offsets,
+                               uint32_t n_docs, void *stream);
+int sj_parse_query(sj_parser *p);
+sj_status sj_parse_batch_wait(sj_parser *p, sj_doc_result *out, const uint32_t **indices,
+                              const uint64_t **tape, const uint8_t **strings);
+
+/* Device memory held by a parser, in bytes. */
+uint64_t sj_parser_device_bytes(const sj_parser *p);
+
+/* ---- Serving: continuous batching ----------------------------------------
+ * The paper parses one document per call; a server parses a stream of
+ * requests.  Requests are queued in arrival order; whenever one of the
+ * server's slots is free, the waiting requests (up to max_batch_bytes and
+ * max_batch_docs) form one batch, launched on that slot's own stream, so
+ * several batches are on the GPU at once.  Results stay in the slot's device
+ * buffers until every document of the batch has been released.  Slots are
+ * created, up to max_slots, while their device memory fits mem_budget
+ * (0 = no budget).  Not thread-safe: one host thread drives a server. */
+typedef struct sj_server sj_server;
+typedef struct {
+  uint64_t mem_budget;       /* device bytes all slots may hold together (0 = unlimited) */
+  uint64_t max_batch_bytes;  /* input bytes per batch; larger requests are refused */
+  uint32_t max_batch_docs;   /* documents per batch */
+  uint32_t max_slots;        /* batches in flight or held, at most */
+  uint32_t max_depth;        /* as in sj_parser_create */
+  uint32_t reserved;
+} sj_server_config;
+
+/* One finished request.  The pointers are device pointers to the document's
+ * own indices, tape and strings (payloads relative to its strings), valid
+ * until sj_server_release(ticket). */
+typedef struct {
+  uint64_t ticket;
+  int32_t error;             /* sj_error of the document */
+  uint32_t slot;
+  uint64_t n_indices, tape_words, string_bytes;
+  const uint32_t *indices;
+  const uint64_t *tape;
+  const uint8_t *strings;
+} sj_completion;
+
+sj_status sj_server_create(sj_server **out, const sj_server_config *cfg);
+void sj_server_destroy(sj_server *s);
+uint32_t sj_server_slots(const sj_server *s);
+uint64_t sj_server_device_bytes(const sj_server *s);
+uint64_t sj_server_batches(const sj_server *s);
+
+/* Queue a request.  The bytes (host memory) are read when its batch is
+ * formed, during a later sj_server_poll, and must stay valid until then.
+ * Writes the request's ticket (consecutive from 0).  SJ_CAPACITY when len is
+ * above max_batch_bytes. */
+sj_status sj_server_submit(sj_server *s, const uint8_t *bytes, uint64_t len, uint64_t *ticket);
+
+/* Collect finished batches, launch waiting requests on free slots, and write
+ * up to max finished requests to out.  Returns their number, or -status. */
+int sj_server_poll(sj_server *s, sj_completion *out, uint32_t max);
+
+/* Give up a finished request's results. */
+sj_status sj_server_release(sj_server *s, uint64_t ticket);
+
+/* Replay an arrival trace: request i (bytes[offsets[i] .. offsets[i+1]),
+ * host memory) is submitted once arrival_s[i] seconds have passed since the
+ * call started (arrival_s non-decreasing); every result is released as soon
+ * as it is seen.  latency_s[i] = the time its result was seen minus
+ * arrival_s[i]; *wall_s = the time until the last result. */
+sj_status sj_server_replay(sj_server *s, const uint8_t *bytes, const uint64_t *offsets,
+                           const double *arrival_s, uint32_t n, double *latency_s,
+                           double *wall_s);
 
 /* Per-kernel timing.  With profiling on, runs launch their kernels directly
  * (not through the captured graph) with CUDA events recorded between them on

@@ -25,7 +25,7 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsj.so")
-_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu"]
+_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu", "server.cpp"]
 _HEADERS = ["sj_internal.cuh", "s1_common.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
@@ -81,6 +81,18 @@ class _DocResult(ctypes.Structure):
                 ("tape_offset", ctypes.c_uint64), ("strings_offset", ctypes.c_uint64)]
 
 
+class _ServerConfig(ctypes.Structure):
+    _fields_ = [("mem_budget", ctypes.c_uint64), ("max_batch_bytes", ctypes.c_uint64),
+                ("max_batch_docs", ctypes.c_uint32), ("max_slots", ctypes.c_uint32),
+                ("max_depth", ctypes.c_uint32), ("reserved", ctypes.c_uint32)]
+
+
+COMPLETION_DTYPE = np.dtype([("ticket", np.uint64), ("error", np.int32), ("slot", np.uint32),
+                             ("n_indices", np.uint64), ("tape_words", np.uint64),
+                             ("string_bytes", np.uint64), ("indices", np.uint64),
+                             ("tape", np.uint64), ("strings", np.uint64)])
+
+
 class _Result(ctypes.Structure):
     _fields_ = [("error", ctypes.c_int32), ("reserved", ctypes.c_uint32),
                 ("n_indices", ctypes.c_uint64), ("tape_words", ctypes.c_uint64),
@@ -131,6 +143,33 @@ def load(path: str | None = None):
     lib.sj_last_cuda_error.restype = ctypes.c_int
     lib.sj_version.argtypes = []
     lib.sj_version.restype = ctypes.c_char_p
+    lib.sj_parse_batch_async.argtypes = [vp, vp, vp, u32, vp]
+    lib.sj_parse_batch_async.restype = ctypes.c_int
+    lib.sj_parse_query.argtypes = [vp]
+    lib.sj_parse_query.restype = ctypes.c_int
+    lib.sj_parse_batch_wait.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
+                                        ctypes.POINTER(vp)]
+    lib.sj_parse_batch_wait.restype = ctypes.c_int
+    lib.sj_parser_device_bytes.argtypes = [vp]
+    lib.sj_parser_device_bytes.restype = u64
+    lib.sj_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_ServerConfig)]
+    lib.sj_server_create.restype = ctypes.c_int
+    lib.sj_server_destroy.argtypes = [vp]
+    lib.sj_server_destroy.restype = None
+    lib.sj_server_slots.argtypes = [vp]
+    lib.sj_server_slots.restype = u32
+    lib.sj_server_device_bytes.argtypes = [vp]
+    lib.sj_server_device_bytes.restype = u64
+    lib.sj_server_batches.argtypes = [vp]
+    lib.sj_server_batches.restype = u64
+    lib.sj_server_submit.argtypes = [vp, vp, u64, ctypes.POINTER(u64)]
+    lib.sj_server_submit.restype = ctypes.c_int
+    lib.sj_server_poll.argtypes = [vp, vp, u32]
+    lib.sj_server_poll.restype = ctypes.c_int
+    lib.sj_server_release.argtypes = [vp, u64]
+    lib.sj_server_release.restype = ctypes.c_int
+    lib.sj_server_replay.argtypes = [vp, vp, vp, vp, u32, vp, ctypes.POINTER(ctypes.c_double)]
+    lib.sj_server_replay.restype = ctypes.c_int
     _lib = lib
     return lib
 
@@ -138,7 +177,10 @@ def load(path: str | None = None):
 EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async", "sj_parse_wait",
             "sj_parse_batch", "sj_parser_set_profiling", "sj_parser_stage_times",
             "sj_parser_kernels_per_run", "sj_stage1_indices_noalloc", "sj_error_name",
-            "sj_last_cuda_error", "sj_version"]
+            "sj_last_cuda_error", "sj_version", "sj_parse_batch_async", "sj_parse_query",
+            "sj_parse_batch_wait", "sj_parser_device_bytes", "sj_server_create",
+            "sj_server_destroy", "sj_server_slots", "sj_server_device_bytes", "sj_server_batches",
+            "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay"]
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
           "s2_build", "finalize")
 
@@ -289,3 +331,83 @@ class Parser:
     @staticmethod
     def view(ptr: int, n: int, typestr: str):
         return _device_tensor(ptr, n, typestr)
+
+    def device_bytes(self) -> int:
+        return int(self._lib.sj_parser_device_bytes(self._h))
+
+
+class Server:
+    """Continuous-batching parse server (sj_server_* of include/sj.h).
+
+    submit() queues host bytes (kept alive here until the request's batch is
+    formed); poll() launches waiting requests on free slots and returns the
+    finished ones as a COMPLETION_DTYPE array, whose pointers stay valid until
+    release(ticket)."""
+
+    def __init__(self, max_batch_bytes: int = 16 << 20, max_batch_docs: int = 4096,
+                 max_slots: int = 8, mem_budget: int = 8 << 30, max_depth: int = 0):
+        self._lib = load()
+        cfg = _ServerConfig(int(mem_budget), int(max_batch_bytes), int(max_batch_docs),
+                            int(max_slots), int(max_depth), 0)
+        h = ctypes.c_void_p()
+        _check(self._lib.sj_server_create(ctypes.byref(h), ctypes.byref(cfg)))
+        self._h = h
+        self._keep = {}
+        self._buf = np.zeros(1024, dtype=COMPLETION_DTYPE)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sj_server_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    @property
+    def slots(self) -> int:
+        return int(self._lib.sj_server_slots(self._h))
+
+    @property
+    def device_bytes(self) -> int:
+        return int(self._lib.sj_server_device_bytes(self._h))
+
+    @property
+    def batches(self) -> int:
+        return int(self._lib.sj_server_batches(self._h))
+
+    def submit(self, data) -> int:
+        b = np.ascontiguousarray(np.frombuffer(data, dtype=np.uint8) if isinstance(data, (bytes, bytearray))
+                                 else data, dtype=np.uint8)
+        t = ctypes.c_uint64()
+        _check(self._lib.sj_server_submit(self._h, b.ctypes.data if b.size else None, b.size,
+                                          ctypes.byref(t)))
+        self._keep[t.value] = b
+        return t.value
+
+    def poll(self) -> np.ndarray:
+        n = self._lib.sj_server_poll(self._h, self._buf.ctypes.data, self._buf.size)
+        if n < 0:
+            _check(-n)
+        out = self._buf[:n].copy()
+        for tk in out["ticket"]:
+            self._keep.pop(int(tk), None)
+        return out
+
+    def release(self, ticket: int):
+        _check(self._lib.sj_server_release(self._h, int(ticket)))
+
+    def replay(self, buf: np.ndarray, offsets: np.ndarray, arrival_s: np.ndarray):
+        """Replay an arrival trace natively; returns (latency_s array, wall seconds)."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        off = np.ascontiguousarray(offsets, dtype=np.uint64)
+        arr = np.ascontiguousarray(arrival_s, dtype=np.float64)
+        n = arr.size
+        lat = np.zeros(n, dtype=np.float64)
+        wall = ctypes.c_double()
+        _check(self._lib.sj_server_replay(self._h, buf.ctypes.data, off.ctypes.data,
+                                          arr.ctypes.data, n, lat.ctypes.data,
+                                          ctypes.byref(wall)))
+        return lat, wall.value

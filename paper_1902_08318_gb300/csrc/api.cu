@@ -5,7 +5,7 @@
 // (reduce, tile scan, frontier, build) and finalize (per-document results),
 // bracketed by a host-to-device copy of the run descriptor and the document
 // offsets and a device-to-host copy of the results.  The sequence is captured
-// once per (parser, document count) as a CUDA graph and replayed.
+// once per (parser, bucket of document counts) as a CUDA graph and replayed.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -77,10 +77,11 @@ struct sj_parser {
   // launch shapes
   int s1_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
   uint32_t scan_blocks = 0, spt_levels = 0;
-  // graph cache
+  uint64_t device_bytes = 0;  // cudaMalloc'ed by this parser
+  // graph cache: one captured run per document-count bucket (powers of two)
+  static constexpr int kBuckets = 33;
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t graph = nullptr;
-  uint32_t graph_docs = 0;
+  cudaGraphExec_t graphs[kBuckets] = {};
   cudaEvent_t done = nullptr;
   static constexpr int kStages = 8;
   cudaEvent_t prof[kStages + 1] = {};
@@ -102,15 +103,18 @@ static int cuda_fail(cudaError_t e) {
   } while (0)
 
 template <class T>
-static int dalloc(T **p, uint64_t n) {
-  CK(cudaMalloc((void **)p, (size_t)(n ? n : 1) * sizeof(T)));
+static int dalloc(sj_parser *p, T **ptr, uint64_t n) {
+  const size_t bytes = (size_t)(n ? n : 1) * sizeof(T);
+  CK(cudaMalloc((void **)ptr, bytes));
+  p->device_bytes += bytes;
   return SJ_SUCCESS;
 }
 
 extern "C" void sj_parser_destroy(sj_parser *p) {
   if (!p) return;
   if (p->pending) cudaEventSynchronize(p->done);
-  if (p->graph) cudaGraphExecDestroy(p->graph);
+  for (cudaGraphExec_t g : p->graphs)
+    if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->done) cudaEventDestroy(p->done);
   for (cudaEvent_t e : p->prof)
@@ -137,39 +141,39 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->max_tiles = max_bytes / sj::kTileBytes + (uint64_t)max_docs + 1;
   const uint64_t tiles = p->max_tiles;
   int r;
-  if ((r = dalloc(&p->d_input, max_bytes + 64))) return r;
-  if ((r = dalloc(&p->d_doc_off, (uint64_t)max_docs + 1))) return r;
-  if ((r = dalloc(&p->d_tile_first, (uint64_t)max_docs + 1))) return r;
-  if ((r = dalloc(&p->d_counters, 4))) return r;
+  if ((r = dalloc(p, &p->d_input, max_bytes + 64))) return r;
+  if ((r = dalloc(p, &p->d_doc_off, (uint64_t)max_docs + 1))) return r;
+  if ((r = dalloc(p, &p->d_tile_first, (uint64_t)max_docs + 1))) return r;
+  if ((r = dalloc(p, &p->d_counters, 4))) return r;
   p->scan_blocks = (uint32_t)((tiles + sj::kScanBlock - 1) / sj::kScanBlock);
   p->spt_levels = 2;
   while ((1ull << (p->spt_levels - 1)) <= tiles) p->spt_levels++;
-  if ((r = dalloc(&p->d_tile_cnt, tiles))) return r;
-  if ((r = dalloc(&p->d_tile_off, tiles))) return r;
-  if ((r = dalloc(&p->d_s1_rec, tiles))) return r;
-  if ((r = dalloc(&p->d_s1_pre, tiles))) return r;
-  if ((r = dalloc(&p->d_s1_blk, tiles * 64))) return r;
-  if ((r = dalloc(&p->d_s2_rec, tiles))) return r;
-  if ((r = dalloc(&p->d_s2_pre, tiles))) return r;
-  if ((r = dalloc(&p->d_scan_agg, p->scan_blocks))) return r;
-  if ((r = dalloc(&p->d_scan_pre, p->scan_blocks))) return r;
-  if ((r = dalloc(&p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
-  if ((r = dalloc(&p->d_slen, max_bytes + 16))) return r;
-  if ((r = dalloc(&p->d_s1_qx, tiles * 32))) return r;
-  if ((r = dalloc(&p->d_meta, max_bytes + 16))) return r;
-  if ((r = dalloc(&p->d_unesc, max_bytes + 64))) return r;
-  if ((r = dalloc(&p->d_front, max_bytes + tiles + 16))) return r;
-  if ((r = dalloc(&p->d_surv, max_bytes + 16))) return r;
-  if ((r = dalloc(&p->d_idx, max_bytes + 16))) return r;
-  if ((r = dalloc(&p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
-  if ((r = dalloc(&p->d_strings, (5 * max_bytes) / 2 + 8ull * max_docs + 64))) return r;
-  if ((r = dalloc(&p->d_doc_flags, max_docs))) return r;
-  if ((r = dalloc(&p->d_doc_nidx, max_docs))) return r;
-  if ((r = dalloc(&p->d_doc_err, max_docs))) return r;
-  if ((r = dalloc(&p->d_doc_tape, max_docs))) return r;
-  if ((r = dalloc(&p->d_doc_str, max_docs))) return r;
-  if ((r = dalloc(&p->d_results, max_docs))) return r;
-  if ((r = dalloc(&p->d_job, 1))) return r;
+  if ((r = dalloc(p, &p->d_tile_cnt, tiles))) return r;
+  if ((r = dalloc(p, &p->d_tile_off, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s1_rec, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s1_pre, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s1_blk, tiles * 64))) return r;
+  if ((r = dalloc(p, &p->d_s2_rec, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s2_pre, tiles))) return r;
+  if ((r = dalloc(p, &p->d_scan_agg, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_pre, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
+  if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
+  if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_unesc, max_bytes + 64))) return r;
+  if ((r = dalloc(p, &p->d_front, max_bytes + tiles + 16))) return r;
+  if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_idx, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
+  if ((r = dalloc(p, &p->d_strings, (5 * max_bytes) / 2 + 8ull * max_docs + 64))) return r;
+  if ((r = dalloc(p, &p->d_doc_flags, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_doc_nidx, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_doc_err, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_doc_tape, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_doc_str, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_results, max_docs))) return r;
+  if ((r = dalloc(p, &p->d_job, 1))) return r;
   CK(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t)));
   CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
   CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
@@ -191,7 +195,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->s2b_grid = sms * (occ2b > 0 ? occ2b : 1);
   // level tables of the reduce warps (zero between tiles)
   const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
-  if ((r = dalloc(&p->d_open_g, open_entries))) return r;
+  if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
   CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
@@ -283,31 +287,42 @@ static uint32_t kernels_per_run(const sj_parser *p) {
          (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 + 1 /* build, finalize */;
 }
 
-// Capture (once per document count) the launch sequence of one run.
-static int ensure_graph(sj_parser *p, uint32_t n_docs) {
-  if (p->graph && p->graph_docs == n_docs) return SJ_SUCCESS;
-  if (p->graph) {
-    cudaGraphExecDestroy(p->graph);
-    p->graph = nullptr;
+// The launch sequence of one run, captured once per bucket of document
+// counts: the kernels read the count from the run descriptor, and the copies
+// of the offsets and results move a whole bucket (the smallest power of two
+// not below the count, at most max_docs).
+static uint32_t bucket_of(const sj_parser *p, uint32_t n_docs, int *b) {
+  int k = 0;
+  while ((1ull << k) < n_docs) k++;
+  *b = k;
+  return (uint32_t)((1ull << k) < p->max_docs ? (1ull << k) : p->max_docs);
+}
+
+static int ensure_graph(sj_parser *p, uint32_t n_docs, cudaGraphExec_t *out) {
+  int b;
+  const uint32_t nb = bucket_of(p, n_docs, &b);
+  if (p->graphs[b]) {
+    *out = p->graphs[b];
+    return SJ_SUCCESS;
   }
   cudaStream_t s = p->cap_stream;
   cudaGraph_t g = nullptr;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
   cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
+  cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)nb + 1) * sizeof(uint64_t),
                   cudaMemcpyHostToDevice, s);
   enqueue_run(p, s, nullptr);
-  cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
+  cudaMemcpyAsync(p->h_results, p->d_results, (size_t)nb * sizeof(sj_doc_result),
                   cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) return cuda_fail(e);
-  e = cudaGraphInstantiate(&p->graph, g, 0);
+  e = cudaGraphInstantiate(&p->graphs[b], g, 0);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
-    p->graph = nullptr;
+    p->graphs[b] = nullptr;
     return cuda_fail(e);
   }
-  p->graph_docs = n_docs;
+  *out = p->graphs[b];
   return SJ_SUCCESS;
 }
 
@@ -350,8 +365,9 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
     CK(cudaGetLastError());
     p->profiled_run = true;
   } else {
-    if ((r = ensure_graph(p, n_docs))) return r;
-    CK(cudaGraphLaunch(p->graph, stream));
+    cudaGraphExec_t g;
+    if ((r = ensure_graph(p, n_docs, &g))) return r;
+    CK(cudaGraphLaunch(g, stream));
     p->profiled_run = false;
   }
   CK(cudaEventRecord(p->done, stream));
@@ -402,11 +418,10 @@ extern "C" sj_status sj_parse(sj_parser *p, const uint8_t *bytes, uint64_t len, 
   return sj_parse_wait(p, out);
 }
 
-extern "C" sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc_offsets,
-                                    uint32_t n_docs, void *stream, sj_doc_result *out,
-                                    const uint32_t **indices, const uint64_t **tape,
-                                    const uint8_t **strings) {
-  if (!p || !doc_offsets || !out || n_docs == 0) return SJ_INVALID_ARG;
+extern "C" sj_status sj_parse_batch_async(sj_parser *p, const uint8_t *bytes,
+                                          const uint64_t *doc_offsets, uint32_t n_docs,
+                                          void *stream) {
+  if (!p || !doc_offsets || n_docs == 0) return SJ_INVALID_ARG;
   if (n_docs > p->max_docs) return SJ_CAPACITY;
   for (uint32_t i = 0; i < n_docs; i++)
     if (doc_offsets[i + 1] < doc_offsets[i]) return SJ_INVALID_ARG;
@@ -422,15 +437,42 @@ extern "C" sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const ui
   static const uint8_t empty[16] = {0};
   if (!total) first = empty;
   (void)dev;
-  if ((r = launch(p, first, total, n_docs, (cudaStream_t)stream))) return r;
+  return launch(p, first, total, n_docs, (cudaStream_t)stream);
+}
+
+extern "C" int sj_parse_query(sj_parser *p) {
+  if (!p) return -SJ_INVALID_ARG;
+  if (!p->pending) return 1;
+  const cudaError_t e = cudaEventQuery(p->done);
+  if (e == cudaSuccess) return 1;
+  if (e == cudaErrorNotReady) return 0;
+  return -cuda_fail(e);
+}
+
+extern "C" sj_status sj_parse_batch_wait(sj_parser *p, sj_doc_result *out, const uint32_t **indices,
+                                         const uint64_t **tape, const uint8_t **strings) {
+  if (!p || !out || !p->pending) return SJ_INVALID_ARG;
+  int r;
   if ((r = wait_pending(p))) return r;
   CK(cudaGetLastError());
-  memcpy(out, p->h_results, (size_t)n_docs * sizeof(sj_doc_result));
+  memcpy(out, p->h_results, (size_t)p->last_docs * sizeof(sj_doc_result));
   if (indices) *indices = p->d_idx;
   if (tape) *tape = p->d_tape;
   if (strings) *strings = p->d_strings;
   return SJ_SUCCESS;
 }
+
+extern "C" sj_status sj_parse_batch(sj_parser *p, const uint8_t *bytes, const uint64_t *doc_offsets,
+                                    uint32_t n_docs, void *stream, sj_doc_result *out,
+                                    const uint32_t **indices, const uint64_t **tape,
+                                    const uint8_t **strings) {
+  if (!out) return SJ_INVALID_ARG;
+  int r = sj_parse_batch_async(p, bytes, doc_offsets, n_docs, stream);
+  if (r) return r;
+  return sj_parse_batch_wait(p, out, indices, tape, strings);
+}
+
+extern "C" uint64_t sj_parser_device_bytes(const sj_parser *p) { return p ? p->device_bytes : 0; }
 
 extern "C" sj_status sj_parser_set_profiling(sj_parser *p, int enable) {
   if (!p) return SJ_INVALID_ARG;

@@ -52,3 +52,14 @@ def test_invalid_arguments_rejected_without_a_gpu():
 def test_no_cpu_fallback_in_the_product_package():
     src = open(os.path.join(ROOT, "paper_1902_08318_gb300", "__init__.py")).read()
     assert "import oracle" not in src and "from oracle" not in src
+
+
+def test_server_calls_reject_invalid_arguments_without_a_gpu():
+    lib = sj.load()
+    assert lib.sj_server_create(None, None) == sj.INVALID_ARG
+    assert lib.sj_server_poll(None, None, 0) == -sj.INVALID_ARG
+    assert lib.sj_server_release(None, 0) == sj.INVALID_ARG
+    assert lib.sj_server_submit(None, None, 0, None) == sj.INVALID_ARG
+    assert lib.sj_server_slots(None) == 0
+    assert lib.sj_parse_query(None) == -sj.INVALID_ARG
+    assert lib.sj_parse_batch_async(None, None, None, 0, None) == sj.INVALID_ARG
