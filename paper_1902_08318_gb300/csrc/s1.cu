@@ -30,28 +30,63 @@ __device__ __forceinline__ uint64_t bs_run_before(const uint8_t *doc, uint64_t e
   }
 }
 
-// UTF-8 check of one 64-byte block whose words are in shared memory (a
-// compact loop: only non-ASCII words, or words continuing a sequence, are
-// walked byte by byte).  `prev` holds the 3 bytes before the block in its top
-// bytes, `nprev` of them inside the document.
-__device__ __noinline__ bool utf8_block_error_smem(const uint32_t *w, uint32_t prev, int nprev,
-                                                   bool doc_ends_here) {
-  Utf8State s{0, 0x80, 0xBF, false};
-  for (int k = 3 - nprev; k < 3; k++) {
-    Utf8State t = s;
-    utf8_step(t, (prev >> (8 * (k + 1))) & 0xFF);
-    if (t.err) t = Utf8State{0, 0x80, 0xBF, false};
-    s = t;
-  }
-#pragma unroll 1
+// UTF-8 check of one 64-byte block (Sec. 3.1.5, Table "tab:unicode").
+// The structure of the sequences is checked on bit masks: the continuation
+// bytes (10xxxxxx) must be exactly the positions that the lead bytes before
+// them require -- one after every 11xxxxxx lead, a second after 111xxxxx, a
+// third after 1111xxxx -- including positions required by leads among the 3
+// bytes before the block (`prev`, top bytes; missing bytes are 0).  The
+// remaining rules of the table concern single values (C0, C1 and F5-FF never
+// occur; after E0, ED, F0 and F4 the next byte has a narrower range) and are
+// checked at each lead byte, read from the block's copy `wb` in shared
+// memory.  A lead whose sequence runs past the block is checked by the next
+// block through its `prev`, or here when the document ends with the block.
+__device__ __forceinline__ bool utf8_block_error_masks(const uint32_t (&w)[16], const uint8_t *wb,
+                                                 uint32_t prev, bool doc_ends_here) {
+  uint32_t cm[2] = {0, 0}, lm[2] = {0, 0}, l3[2] = {0, 0}, l4[2] = {0, 0};
+#pragma unroll
   for (int j = 0; j < 16; j++) {
-    const uint32_t x = w[j];
-    if ((x & 0x80808080u) == 0 && s.need == 0) continue;
-#pragma unroll 1
-    for (int b = 0; b < 4; b++) utf8_step(s, (x >> (8 * b)) & 0xFF);
+    const uint32_t x = w[j], x1 = x << 1, x2 = x << 2, x3 = x << 3, t = x & x1;
+    const int h = j >> 3, sh = (j & 7) * 4;
+    cm[h] |= movemask4(x & ~x1 & 0x80808080u) << sh;
+    lm[h] |= movemask4(t & 0x80808080u) << sh;
+    l3[h] |= movemask4(t & x2 & 0x80808080u) << sh;
+    l4[h] |= movemask4(t & x2 & x3 & 0x80808080u) << sh;
   }
-  if (doc_ends_here && s.need) s.err = true;
-  return s.err;
+  const uint64_t C = ((uint64_t)cm[1] << 32) | cm[0], L = ((uint64_t)lm[1] << 32) | lm[0];
+  const uint64_t L3 = ((uint64_t)l3[1] << 32) | l3[0], L4 = ((uint64_t)l4[1] << 32) | l4[0];
+  // leads among the bytes before the block (bit 3 = byte -1, 2 = -2, 1 = -3)
+  const uint32_t pt = prev & (prev << 1);
+  const uint32_t pl = movemask4(pt & 0x80808080u), pl3 = movemask4(pt & (prev << 2) & 0x80808080u);
+  const uint32_t pl4 = movemask4(pt & (prev << 2) & (prev << 3) & 0x80808080u);
+  const uint64_t req_in = ((pl >> 3) & 1u) | ((pl3 >> 2) & 2u) | ((pl4 >> 1) & 4u) |  // lead at -1
+                          ((pl3 >> 2) & 1u) | ((pl4 >> 1) & 2u) |                    // lead at -2
+                          ((pl4 >> 1) & 1u);                                         // lead at -3
+  const uint64_t REQ = (L << 1) | (L3 << 2) | (L4 << 3) | req_in;
+  if (C != REQ) return true;
+  if (doc_ends_here && ((L >> 63) | (L3 >> 62) | (L4 >> 61))) return true;
+  // value rules
+  const uint32_t pb = prev >> 24;  // byte -1
+  if (pb == 0xE0 || pb == 0xED || pb == 0xF0 || pb == 0xF4) {
+    const uint32_t b0 = w[0] & 0xFFu;
+    if ((pb == 0xE0 && b0 < 0xA0) || (pb == 0xED && b0 > 0x9F) || (pb == 0xF0 && b0 < 0x90) ||
+        (pb == 0xF4 && b0 > 0x8F))
+      return true;
+  }
+  uint64_t lead = L;
+  while (lead) {
+    const int i = __ffsll((long long)lead) - 1;
+    lead &= lead - 1;
+    const uint32_t b = wb[i];
+    if (b < 0xC2 || b > 0xF4) return true;
+    if (i < 63 && (b == 0xE0 || b == 0xED || b == 0xF0 || b == 0xF4)) {
+      const uint32_t nb = wb[i + 1];
+      if ((b == 0xE0 && nb < 0xA0) || (b == 0xED && nb > 0x9F) || (b == 0xF0 && nb < 0x90) ||
+          (b == 0xF4 && nb > 0x8F))
+        return true;
+    }
+  }
+  return false;
 }
 
 // How the byte before a tile makes its first byte a token start.
@@ -59,7 +94,7 @@ enum : uint32_t { kSepNever = 0, kSepAlways = 1, kSepIfOutside = 2 };
 
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ uint32_t s_words[kS1Warps * 32][17];  // one block per thread, padded
+  __shared__ uint32_t s_words[kS1Warps * 32][16];  // one block per thread (byte reads)
   const int lane = threadIdx.x & 31;
   uint32_t *my_words = s_words[threadIdx.x];
   const uint32_t n_tiles = J.counters[2];
@@ -91,7 +126,8 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
       if (blk < len && need) {
 #pragma unroll
         for (int k = 0; k < 16; k++) my_words[k] = w[k];
-        if (utf8_block_error_smem(my_words, prev, nprev, ends_here)) atomicOr(&J.doc_flags[d], kFlagUtf8);
+        if (utf8_block_error_masks(w, reinterpret_cast<const uint8_t *>(my_words), prev, ends_here))
+          atomicOr(&J.doc_flags[d], kFlagUtf8);
       }
     }
 

@@ -37,6 +37,7 @@ constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
 constexpr int kOpenSmem = 512;                 // levels kept in shared memory (mod 512)
 constexpr int kStrStage = 3328;                // string output of 32 strings, staged
 constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
+constexpr uint32_t kFrontSmem = 64;            // frontier slots of a tile kept in shared memory
 
 // A string's entry in `slen`: an error code, or its normalised length and
 // whether it holds escapes (then the reduce pass has left its normalised bytes
@@ -111,8 +112,11 @@ __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc,
 // document's end after its last token), with the next chunk prefetched.
 struct Positions {
   uint32_t pos_next = 0;
-  __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt, int lane) {
+  uint32_t after = 0;  // (lane 0) the position after the tile's last token, loaded up front
+  __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt,
+                                        uint32_t nidx, uint64_t len, int lane) {
     pos_next = (uint32_t)lane < cnt ? idxp[off + lane] : 0u;
+    if (lane == 0) after = off + cnt < nidx ? idxp[off + cnt] : (uint32_t)len;
   }
   __device__ __forceinline__ void next(uint32_t &pos, uint32_t &nxt, const uint32_t *idxp,
                                        uint32_t off, uint32_t cnt, uint32_t nidx, uint64_t len,
@@ -123,11 +127,11 @@ struct Positions {
     pos_next = jn < cnt ? idxp[off + jn] : 0u;
     uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, pos, 1);
     const uint32_t first_next = __shfl_sync(0xFFFFFFFFu, pos_next, 0);
-    if (lane == 31 || j + 1 == cnt) {
-      const uint32_t g = off + j + 1;  // document index of the next token
-      nx = (j + 1 < cnt) ? first_next : (g < nidx ? idxp[g] : (uint32_t)len);
-    }
+    const uint32_t aft = __shfl_sync(0xFFFFFFFFu, after, 0);
+    if (lane == 31 || j + 1 == cnt) nx = (j + 1 < cnt) ? first_next : aft;
     nxt = nx;
+    (void)nidx;
+    (void)len;
   }
 };
 
@@ -288,7 +292,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     };
 
     Positions ps;
-    ps.begin(idxp, off, cnt, lane);
+    ps.begin(idxp, off, cnt, nidx, len, lane);
     int32_t depth = 0, mn = 0, mx = 0;
     uint32_t tape = 0;
     for (uint32_t base = 0; base < cnt; base += 32) {
@@ -380,6 +384,7 @@ struct __align__(16) BuildSmem {
   QEntry nq[kQueue];        // numbers awaiting conversion
   QEntry sq[kQueue];        // strings awaiting output
   WQEntry wq[kQueue];       // strings with escapes awaiting output
+  uint64_t front[kFrontSmem];  // the first frontier slots of the tile
 };
 static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
               "per-warp staging must stay 16-byte aligned");
@@ -459,6 +464,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       J.doc_str[d] = pre.str_start + agg.s;
     }
 
+    // the tile's frontier slots: the container open at each level the tile
+    // starts inside, deepest first (levels d_start down to max(1, low))
+    const uint32_t nfront = pre.d_start >= max(1, pre.low) ? (uint32_t)(pre.d_start - max(1, pre.low) + 1) : 0u;
+    for (uint32_t k = lane; k < min(nfront, kFrontSmem); k += 32) W.front[k] = front[k];
     const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
     uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0, whead = 0, wtail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
@@ -568,8 +577,11 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     };
 
     Positions ps;
-    ps.begin(idxp, off, cnt, lane);
+    ps.begin(idxp, off, cnt, nidx, len, lane);
+    // token facts and string entries are loaded one chunk ahead (the string
+    // entry for every lane: a coalesced load, used only by strings)
     uint64_t meta_next = (uint32_t)lane < cnt ? J.meta[ib + off + lane] : 0ull;
+    uint32_t sl_next = (uint32_t)lane < cnt ? J.slen[ib + off + lane] : 0u;
     // kinds of the two tokens before the tile
     uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
     if (lane < 2 && off >= (uint32_t)lane + 1) {
@@ -584,9 +596,11 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       uint32_t pos, nxt;
       ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
       const uint64_t meta = meta_next;
+      const uint32_t sl_all = sl_next;
       meta_next = j + 32 < cnt ? J.meta[ib + off + j + 32] : 0ull;
+      sl_next = j + 32 < cnt ? J.slen[ib + off + j + 32] : 0u;
       const uint8_t k = (uint8_t)(meta & 15u);
-      const uint32_t sl = (valid && k == K_STRING) ? J.slen[ib + off + j] : 0u;
+      const uint32_t sl = (valid && k == K_STRING) ? sl_all : 0u;
       const int32_t E = pre.d_start + ((int32_t)((meta >> 4) & 0x1FFFu) - 4096);
       const uint32_t trel = (uint32_t)(meta >> 17) & 0x1FFFu;
       const uint64_t tp = (uint64_t)pre.tape_start + trel;
@@ -608,7 +622,8 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
           K = (parent & 0x4000u) ? K_OPEN_OBJ : K_OPEN_ARR;
           par_tape = (uint64_t)pre.tape_start + (parent & 0x0FFFu);
         } else if (E >= max(1, pre.low) && E <= pre.d_start) {
-          const uint64_t ent = front[pre.d_start - E];
+          const uint32_t fk = (uint32_t)(pre.d_start - E);
+          const uint64_t ent = fk < kFrontSmem ? W.front[fk] : front[fk];
           if (ent != ~0ull) {
             K = (ent >> 63) ? K_OPEN_OBJ : K_OPEN_ARR;
             par_tape = ent & 0xFFFFFFFFull;
