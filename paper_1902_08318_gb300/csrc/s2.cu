@@ -32,7 +32,8 @@ __device__ __forceinline__ void report(const Job &J, uint32_t d, uint64_t token,
 constexpr int kS2Warps = kS2Threads / 32;
 constexpr int kHalo = 1024;                    // staged bytes past the tile's end
 constexpr int kStageBytes = kTileBytes + kHalo;
-constexpr int kStageBlocks = kStageBytes / kBlockBytes;
+constexpr int kStageBytesR = kTileBytes + 512;  // the reduce pass stages a shorter halo
+constexpr int kStageBlocksR = kStageBytesR / kBlockBytes;
 constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
 constexpr int kOpenSmem = 512;                 // levels kept in shared memory (mod 512)
 constexpr int kStrStage = 3328;                // string output of 32 strings, staged
@@ -89,12 +90,13 @@ struct Staged {
 };
 
 // Copy the tile's bytes and kHalo more (16-byte chunks) into shared memory.
+template <int STAGE = kStageBytes>
 __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc, uint64_t len,
                                              uint64_t t0, int lane) {
   const uintptr_t g0 = (uintptr_t)(doc + t0);
   const uintptr_t a0 = g0 & ~(uintptr_t)15;
   const uintptr_t dend = (uintptr_t)doc + len;
-  const uintptr_t send = min((uintptr_t)(a0 + kStageBytes), dend);
+  const uintptr_t send = min((uintptr_t)(a0 + STAGE), dend);
   const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
   for (uint32_t c = lane; c < nch; c += 32)
     reinterpret_cast<uint4 *>(bytes)[c] = __ldg(reinterpret_cast<const uint4 *>(a0 + 16 * c));
@@ -142,12 +144,15 @@ struct QEntry {
   uint32_t pos, nxt, j, tp;  // position, next token's position, index and tape slot in the tile
   uint32_t sl;               // a string's `slen` entry
 };
-struct WQEntry {
-  uint64_t so;               // buffer offset of the string's entry
-  uint32_t p0, n;            // first content byte, normalised length
-};
+
 struct RQEntry {
   uint32_t pos, nxt, j;
+};
+struct RWEntry {     // a string with escapes, kept across tiles until 32 are queued
+  uint64_t a;        // its first content byte, as an offset from the batch base
+  uint64_t slot;     // its `slen` slot
+  uint32_t n;        // bytes from there to the next token
+  uint32_t tile;     // the tile whose string-buffer total it belongs to
 };
 
 template <class T>
@@ -164,11 +169,11 @@ __device__ __forceinline__ void enqueue(T *q, uint32_t &tail, bool take, const T
 // normalised length of each string.
 // ---------------------------------------------------------------------------
 struct __align__(16) ReduceSmem {  // 16-byte aligned size: bytes[] takes uint4 stores
-  uint8_t bytes[kStageBytes + 64];
-  uint64_t q[kStageBlocks];        // real quotes of the staged blocks
-  uint64_t x[kStageBlocks];        // backslash and control bytes of the staged blocks
+  uint8_t bytes[kStageBytesR + 64];
+  uint64_t q[kStageBlocksR];       // real quotes of the staged blocks
+  uint64_t x[kStageBlocksR];       // backslash and control bytes of the staged blocks
   RQEntry sq[kQueue];              // strings awaiting their length
-  RQEntry wq[kQueue];              // strings with escapes awaiting a walk
+  RWEntry wq[kQueue];              // strings with escapes awaiting a walk
   uint16_t open[kOpenSmem];
 };
 static_assert(sizeof(ReduceSmem) % 16 == 0, "per-warp staging must stay 16-byte aligned");
@@ -221,6 +226,36 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
   uint16_t *const open_g = J.open_g + (uint64_t)(blockIdx.x * kS2Warps + wid) * kOpenGlobal;
   const uint32_t n_tiles = J.counters[2];
   const uint32_t warps = gridDim.x * kS2Warps;
+  // Strings with escapes are walked (Sec. 3.2.2) 32 at a time, across tiles:
+  // a tile holds too few of them to fill a warp.  The walk reads the staged
+  // bytes while its string is in the current tile, else global memory, and
+  // adds the string's buffer bytes to its own tile's total.
+  uint32_t whead = 0, wtail = 0;
+  uint64_t stg_lo = 1, stg_hi = 0;  // staged bytes of the current tile, as batch offsets
+  auto flush_walks = [&]() {
+    const uint32_t m = min(32u, wtail - whead);
+    if ((uint32_t)lane < m) {
+      const RWEntry e = W.wq[(whead + lane) & (kQueue - 1)];
+      const uint8_t *sp = (e.a >= stg_lo && e.a + e.n <= stg_hi) ? W.bytes + (e.a - stg_lo)
+                                                                 : J.base + e.a;
+      int err;
+      // normalised bytes are never more than the raw ones: they stay within
+      // the string's own span of the scratch buffer
+      const uint32_t n = string_walk<true>(sp, sp + e.n, err, J.unesc + (e.a - J.doc_off[0]));
+      uint64_t size;
+      if (err) {
+        J.slen[e.slot] = kSlenErr | (uint32_t)err;
+        size = 5;
+      } else {
+        J.slen[e.slot] = kSlenWalk | min(n, kSlenLen);
+        size = 5ull + n;
+      }
+      atomicAdd(reinterpret_cast<unsigned long long *>(&J.s2_rec[e.tile].s),
+                (unsigned long long)size);
+    }
+    whead += m;
+    __syncwarp();
+  };
   for (uint32_t t = blockIdx.x * kS2Warps + wid; t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
@@ -230,6 +265,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
       if (lane == 0) J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
       continue;
     }
+    if (lane == 0) J.s2_rec[t].s = 0;  // walks add to it, from this tile on
     const uint32_t ntiles_d = J.tile_first[d + 1] - j_min;
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
     const uint8_t *doc = J.base + J.doc_off[d];
@@ -237,20 +273,21 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
     uint32_t *slen = J.slen + ib + off;
-    uint8_t *unesc = J.unesc + rel_off(J, d);
     const uint64_t t0 = (uint64_t)tt * kTileBytes;
     // masks of the tile's blocks and of the next ones in the document
-    const uint32_t nblk = min((uint32_t)kStageBlocks, (ntiles_d - tt) * 32u);
+    const uint32_t nblk = min((uint32_t)kStageBlocksR, (ntiles_d - tt) * 32u);
     for (uint32_t k = lane; k < nblk; k += 32) {
       const ulonglong2 v = J.s1_qx[(uint64_t)t * 32 + k];
       W.q[k] = v.x;
       W.x[k] = v.y;
     }
-    const Staged sv = stage_tile(W.bytes, doc, len, t0, lane);
+    const Staged sv = stage_tile<kStageBytesR>(W.bytes, doc, len, t0, lane);
+    stg_lo = J.doc_off[d] + (uint64_t)sv.sbase;
+    stg_hi = J.doc_off[d] + sv.slimit;
     const OpenTable ot = cnt < (uint32_t)kOpenSmem ? OpenTable{W.open, (uint32_t)kOpenSmem - 1u, 0}
                                                    : OpenTable{open_g, 0xFFFFFFFFu, kLevelOff};
-    uint64_t sb = 0;  // string-buffer bytes of this lane's strings
-    uint32_t shead = 0, stail = 0, whead = 0, wtail = 0;
+    uint64_t sb = 0;  // string-buffer bytes of this lane's strings without escapes
+    uint32_t shead = 0, stail = 0;
     // strings: the next 32 queued get their length from the masks; those the
     // masks cannot decide go to the walk queue
     auto flush_strings = [&]() {
@@ -264,30 +301,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
         slen[e.j] = L;
         sb += 5u + L;
       }
-      enqueue(W.wq, wtail, have && !ok, e, lane);
+      enqueue(W.wq, wtail, have && !ok,
+              RWEntry{J.doc_off[d] + e.pos + 1, ib + off + e.j, e.nxt - (e.pos + 1), t}, lane);
       shead += m;
-      __syncwarp();
-    };
-    // strings with escapes: walk them (Sec. 3.2.2), 32 at a time
-    auto flush_walks = [&]() {
-      const uint32_t m = min(32u, wtail - whead);
-      if ((uint32_t)lane < m) {
-        const RQEntry e = W.wq[(whead + lane) & (kQueue - 1)];
-        const uint64_t p0 = (uint64_t)e.pos + 1, p1 = e.nxt;
-        const uint8_t *sp = sv.ptr(p0, p1);
-        int err;
-        // normalised bytes are never more than the raw ones: they stay within
-        // the string's own span of the scratch buffer
-        const uint32_t n = string_walk<true>(sp, sp + (p1 - p0), err, unesc + p0);
-        if (err) {
-          slen[e.j] = kSlenErr | (uint32_t)err;
-          sb += 5u;
-        } else {
-          slen[e.j] = kSlenWalk | min(n, kSlenLen);
-          sb += 5ull + n;
-        }
-      }
-      whead += m;
       __syncwarp();
     };
 
@@ -355,7 +371,6 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
       flush_strings();
       if (wtail - whead >= 32) flush_walks();
     }
-    while (whead != wtail) flush_walks();
 #pragma unroll
     for (int o = 16; o; o >>= 1) {
       sb += __shfl_xor_sync(0xFFFFFFFFu, sb, o);
@@ -371,8 +386,16 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     // forget this tile's levels
     for (int32_t v = max(mn, -kLevelOff) + lane; v <= min(mx, kLevelOff); v += 32) ot.at(v) = 0;
     __syncwarp();
-    if (lane == 0) J.s2_rec[t] = S2Agg{depth, mn, tape, tt == 0, sb};
+    if (lane == 0) {
+      S2Agg &a = J.s2_rec[t];
+      a.dd = depth;
+      a.mn = mn;
+      a.w = tape;
+      a.head = tt == 0;
+      atomicAdd(reinterpret_cast<unsigned long long *>(&a.s), (unsigned long long)sb);
+    }
   }
+  while (whead != wtail) flush_walks();
 }
 
 // ---------------------------------------------------------------------------
@@ -380,10 +403,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
 // ---------------------------------------------------------------------------
 struct __align__(16) BuildSmem {
   uint8_t bytes[kStageBytes + 64];
+  uint8_t ubytes[kStageBytes + 64];  // the same window of the scratch buffer (escaped strings)
   uint8_t sout[kStrStage];  // the string-buffer bytes of 32 strings, before a coalesced copy
   QEntry nq[kQueue];        // numbers awaiting conversion
   QEntry sq[kQueue];        // strings awaiting output
-  WQEntry wq[kQueue];       // strings with escapes awaiting output
   uint64_t front[kFrontSmem];  // the first frontier slots of the tile
 };
 static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
@@ -469,8 +492,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     const uint32_t nfront = pre.d_start >= max(1, pre.low) ? (uint32_t)(pre.d_start - max(1, pre.low) + 1) : 0u;
     for (uint32_t k = lane; k < min(nfront, kFrontSmem); k += 32) W.front[k] = front[k];
     const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
-    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0, whead = 0, wtail = 0;
+    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
+    Staged us{};  // the scratch window, staged at the first string with escapes
+    bool us_staged = false;
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
     // numbers (Sec. 3.2.1), 32 at a time
@@ -523,14 +548,15 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       const uint64_t so = str_run + incl - size;
       const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
       if (is_str && tp < tape_cap) tape[tp] = ((uint64_t)'"' << 56) | so;
-      // Strings with escapes take their normalised bytes from the scratch buffer
-      // of the reduce pass, in flush_walks; the copy below leaves their bytes
-      // undefined until then.
-      enqueue(W.wq, wtail, is_str && walk,
-              WQEntry{so, (uint32_t)p0, (uint32_t)min(n, (uint64_t)0xFFFFFFFFu)}, lane);
-      const bool plain = is_str && !walk;
-      const bool fits = !plain || p0 + n <= sv.slimit;
-      const unsigned sm = __ballot_sync(0xFFFFFFFFu, plain);
+      // Strings with escapes take their normalised bytes from the scratch
+      // buffer of the reduce pass (same positions), staged once per tile.
+      if (!us_staged && __any_sync(0xFFFFFFFFu, is_str && walk)) {
+        us = stage_tile(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
+        us_staged = true;
+      }
+      const Staged &src = walk ? us : sv;
+      const bool fits = !is_str || (n < kSlenLen && p0 + n <= src.slimit);
+      const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
       if (sm) {
         const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
         const uint64_t so_lo = __shfl_sync(0xFFFFFFFFu, so, __ffs(sm) - 1);
@@ -538,7 +564,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
         const uint64_t total = a + (so_hi - so_lo);
         if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (plain) put_string(W.sout + a + (so - so_lo), (uint32_t)n, sv.smem + (p0 - sv.sbase));
+          if (is_str) put_string(W.sout + a + (so - so_lo), (uint32_t)n, src.smem + (p0 - src.sbase));
           __syncwarp();
           uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
           const uint32_t units = (uint32_t)((total + 15) >> 4);
@@ -550,29 +576,12 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
               for (uint32_t i = max(lo, a); i < min(hi, (uint32_t)total); i++) gb[i] = W.sout[i];
             }
           }
-        } else if (plain && so + 5 + n <= str_cap) {
-          put_string(strs + so, (uint32_t)n, sv.ptr(p0, p0 + n));
+        } else if (is_str && so + 5 + n <= str_cap) {
+          put_string(strs + so, (uint32_t)n, walk ? unesc + p0 : sv.ptr(p0, p0 + n));
         }
       }
       str_run += __shfl_sync(0xFFFFFFFFu, incl, 31);
       shead += m;
-      __syncwarp();
-    };
-
-    // Strings with escapes, up to 32: the scratch bytes around the tile are
-    // staged in sout, then the warp copies one string at a time.
-    auto flush_walks = [&]() {
-      const uint32_t m = min(32u, wtail - whead);
-      const Staged us = stage_tile(W.sout, unesc, len, (uint64_t)tt * kTileBytes, lane);
-      for (uint32_t i = 0; i < m; i++) {
-        const WQEntry e = W.wq[(whead + i) & (kQueue - 1)];
-        if (e.so + 5 + e.n > str_cap) continue;
-        const uint8_t *src = us.ptr(e.p0, (uint64_t)e.p0 + e.n);
-        uint8_t *dst = strs + e.so;
-        for (uint32_t b = lane; b < e.n + 5; b += 32)
-          dst[b] = b < 4 ? (uint8_t)(e.n >> (8 * b)) : (b < e.n + 4 ? src[b - 4] : (uint8_t)0);
-      }
-      whead += m;
       __syncwarp();
     };
 
@@ -670,17 +679,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel, sl}, lane);
       __syncwarp();
       if (ntail - nhead >= 32) flush_numbers();
-      if (stail - shead >= 32) {
-        flush_strings();
-        if (wtail - whead >= 32) flush_walks();
-      }
+      if (stail - shead >= 32) flush_strings();
     }
     while (nhead != ntail) flush_numbers();
-    while (shead != stail) {
-      flush_strings();
-      if (wtail - whead >= 32) flush_walks();
-    }
-    while (whead != wtail) flush_walks();
+    while (shead != stail) flush_strings();
     __syncwarp();  // every lane is done with this tile's staged bytes
   }
 }

@@ -235,12 +235,17 @@ __global__ void jump_kernel(const Job *__restrict__ job) {
 // there is none (an invalid document).  Level L of tile t is stored at
 // front[idx_base + tile_off[t] + t + (d_start - L)]: a tile needs at most one
 // more level than it has tokens, and the global tile index keeps documents
-// apart.
+// apart.  One warp per tile: the nearest earlier tile whose lowest depth is
+// below a level holds that level's container among its survivors, and one
+// such tile serves the whole range of levels down to its own lowest depth,
+// so the warp walks the chain of those tiles (jump pointers) once and copies
+// each range with all lanes.
 __global__ void frontier_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   const uint32_t n = J.counters[2];
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+  const int lane = threadIdx.x & 31;
+  const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
+  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nw) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     if (J.doc_flags[d] & (kFlagUtf8 | kFlagUnclosed | kFlagCapacity)) continue;
@@ -251,18 +256,26 @@ __global__ void frontier_kernel(const Job *__restrict__ job) {
     uint64_t *out = J.front + ib + J.tile_off[t] + t;
     int64_t c = (int64_t)t - 1;
     int32_t clow = c >= (int64_t)j_min ? J.s2_pre[c].low : 0;
-    for (int32_t lev = hi; lev >= lo; lev--) {
+    int32_t lev = hi;
+    while (lev >= lo) {
       while (c >= (int64_t)j_min && clow >= lev) {
         const uint32_t jp = J.s2_pre[c].jump;
         c = jp == kNoTile ? -1 : (int64_t)jp;
         if (c >= (int64_t)j_min) clow = J.s2_pre[c].low;
       }
-      uint64_t ent = ~0ull;
-      if (c >= (int64_t)j_min) {
-        const uint32_t e = J.surv[ib + J.tile_off[c] + (uint32_t)(lev - clow - 1)];
-        ent = ((uint64_t)(e >> 31) << 63) | (uint64_t)(J.s2_pre[c].tape_start + (e & 0xFFFFu));
+      if (c >= (int64_t)j_min) {  // levels (clow, lev] come from tile c's survivors
+        const int32_t bottom = max(lo, clow + 1);
+        const uint32_t *sv = J.surv + ib + J.tile_off[c];
+        const uint64_t ts = J.s2_pre[c].tape_start;
+        for (int32_t L = lev - lane; L >= bottom; L -= 32) {
+          const uint32_t e = sv[L - clow - 1];
+          out[hi - L] = ((uint64_t)(e >> 31) << 63) | (ts + (e & 0xFFFFu));
+        }
+        lev = bottom - 1;
+      } else {  // no container: an invalid document
+        for (int32_t L = lev - lane; L >= lo; L -= 32) out[hi - L] = ~0ull;
+        lev = lo - 1;
       }
-      out[hi - lev] = ent;
     }
   }
 }
