@@ -199,6 +199,10 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         raise SystemExit(f"benchmark document rejected: {r.error_name}")
     S, T, SB = r.n_indices, r.tape_words, r.string_bytes
     lex = lexeme_bytes(doc_dev, r.indices()[: S])
+    # launch shapes: the autotuner times each main kernel at every allowed
+    # shape on this document (outside the timed region)
+    tuned = None if args.no_autotune else parser.autotune(doc_dev, stream=stream)
+    launch = parser.launch()
 
     # ---- device-timed region ------------------------------------------------
     parser.set_profiling(True)
@@ -236,8 +240,12 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         ms_e2e, e2e_steps = e2e_leg(parser, doc, stream, args, dev, dist)
     if rank != 0:
         return None
-    return report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_steps, clk,
-                  parser.kernels_per_run())
+    out = report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_steps, clk,
+                 parser.kernels_per_run())
+    out["launch"] = {"blocks_per_sm": {k: c for k, (c, _) in launch.items()},
+                     "max_blocks_per_sm": {k: m for k, (_, m) in launch.items()},
+                     "autotuned": tuned is not None}
+    return out
 
 
 def e2e_leg(parser, doc, stream, args, dev, dist):
@@ -470,6 +478,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config3) leg")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (config4) leg")
     ap.add_argument("--doc-mb", type=int, default=0,
                     help="config2 document size in MiB (default 1024; smaller for ncu captures)")

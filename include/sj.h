@@ -225,6 +225,25 @@ sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
 /* Number of kernel launches in one run of this parser. */
 int sj_parser_kernels_per_run(const sj_parser *p);
 
+/* Launch shapes.  The four main kernels (stage-1 blocks, stage-1 flatten,
+ * stage-2 reduce, stage-2 build) loop over tiles, so any grid covers any
+ * input; the shape is the number of resident blocks per SM, from 1 to the
+ * kernel's occupancy limit (max_blocks_per_sm, may be NULL).  A parser starts
+ * with every kernel at its limit.  sj_parser_set_launch drops the captured
+ * graphs (the next run captures again).  The paper has no counterpart: its
+ * single-threaded parser has no launch shape. */
+sj_status sj_parser_get_launch(const sj_parser *p, uint32_t *blocks_per_sm,
+                               uint32_t *max_blocks_per_sm);
+sj_status sj_parser_set_launch(sj_parser *p, const uint32_t *blocks_per_sm);
+
+/* Autotuner: parses the sample (bytes, len; host or device) to time each of
+ * the four main kernels at every allowed shape, one kernel at a time (reps
+ * timed runs each, after one warm-up), keeps the fastest and writes the
+ * choice and its kernel time (ms) to blocks_per_sm[4] / best_ms[4] (either may
+ * be NULL).  Leaves profiling as it was.  Synchronous on `stream`. */
+sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream,
+                             int reps, uint32_t *blocks_per_sm, float *best_ms);
+
 /* Stage 1 only (structural indices) of one document, allocating nothing.
  * The paper has no counterpart: this entry exists for callers that cannot call
  * cudaMalloc when they parse (device memory owned by another allocator, or a

@@ -150,6 +150,12 @@ def load(path: str | None = None):
     lib.sj_parse_batch_wait.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
     lib.sj_parse_batch_wait.restype = ctypes.c_int
+    lib.sj_parser_get_launch.argtypes = [vp, vp, vp]
+    lib.sj_parser_get_launch.restype = ctypes.c_int
+    lib.sj_parser_set_launch.argtypes = [vp, vp]
+    lib.sj_parser_set_launch.restype = ctypes.c_int
+    lib.sj_parser_autotune.argtypes = [vp, vp, u64, vp, ctypes.c_int, vp, vp]
+    lib.sj_parser_autotune.restype = ctypes.c_int
     lib.sj_parser_device_bytes.argtypes = [vp]
     lib.sj_parser_device_bytes.restype = u64
     lib.sj_server_create.argtypes = [ctypes.POINTER(vp), ctypes.POINTER(_ServerConfig)]
@@ -180,7 +186,9 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_last_cuda_error", "sj_version", "sj_parse_batch_async", "sj_parse_query",
             "sj_parse_batch_wait", "sj_parser_device_bytes", "sj_server_create",
             "sj_server_destroy", "sj_server_slots", "sj_server_device_bytes", "sj_server_batches",
-            "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay"]
+            "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay",
+            "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune"]
+TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
           "s2_build", "finalize")
 
@@ -334,6 +342,28 @@ class Parser:
 
     def device_bytes(self) -> int:
         return int(self._lib.sj_parser_device_bytes(self._h))
+
+    def launch(self) -> dict:
+        """Resident blocks per SM of the four main kernels, and their limits."""
+        cur = np.zeros(4, dtype=np.uint32)
+        lim = np.zeros(4, dtype=np.uint32)
+        _check(self._lib.sj_parser_get_launch(self._h, cur.ctypes.data, lim.ctypes.data))
+        return {k: (int(c), int(m)) for k, c, m in zip(TUNED_KERNELS, cur, lim)}
+
+    def set_launch(self, blocks_per_sm):
+        b = np.ascontiguousarray(blocks_per_sm, dtype=np.uint32)
+        _check(self._lib.sj_parser_set_launch(self._h, b.ctypes.data))
+
+    def autotune(self, sample, stream=None, reps: int = 2) -> dict:
+        """Pick each main kernel's blocks per SM by timing it on `sample`."""
+        ptr, n, keep = _as_input(sample)
+        bps = np.zeros(4, dtype=np.uint32)
+        ms = np.zeros(4, dtype=np.float32)
+        _check(self._lib.sj_parser_autotune(self._h, ptr, n, _stream_handle(stream), int(reps),
+                                            bps.ctypes.data, ms.ctypes.data))
+        del keep
+        return {k: {"blocks_per_sm": int(b), "ms": round(float(t), 4)}
+                for k, b, t in zip(TUNED_KERNELS, bps, ms)}
 
 
 class Server:

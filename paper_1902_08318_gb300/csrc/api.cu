@@ -75,7 +75,9 @@ struct sj_parser {
   uint64_t *h_doc_off = nullptr;
   sj_doc_result *h_results = nullptr;
   // launch shapes
-  int s1_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
+  int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
+  int sms = 0;
+  int occ[4] = {1, 1, 1, 1};  // most resident blocks per SM: s1 blocks, flatten, reduce, build
   uint32_t scan_blocks = 0, spt_levels = 0;
   uint64_t device_bytes = 0;  // cudaMalloc'ed by this parser
   // graph cache: one captured run per document-count bucket (powers of two)
@@ -182,17 +184,26 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
 
-  int sms = 0, occ1 = 0, occ2r = 0, occ2b = 0;
+  int sms = 0, occ1 = 0, occf = 0, occ2r = 0, occ2b = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_blocks_kernel,
+                                                   32 * sj::kS1Warps, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, sj::stage1_flatten_kernel,
                                                    32 * sj::kS1Warps, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2r, sj::stage2_reduce_kernel,
                                                    sj::kS2Threads, 0));
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2b, sj::stage2_build_kernel,
                                                    sj::kS2Threads, 0));
-  p->s1_grid = sms * (occ1 > 0 ? occ1 : 1);
-  p->s2r_grid = sms * (occ2r > 0 ? occ2r : 1);
-  p->s2b_grid = sms * (occ2b > 0 ? occ2b : 1);
+  p->sms = sms;
+  p->occ[0] = occ1 > 0 ? occ1 : 1;
+  p->occ[1] = occf > 0 ? occf : 1;
+  p->occ[2] = occ2r > 0 ? occ2r : 1;
+  p->occ[3] = occ2b > 0 ? occ2b : 1;
+  // default launch: every SM full (the grids are grid-stride loops over tiles)
+  p->s1_grid = sms * p->occ[0];
+  p->fl_grid = sms * p->occ[1];
+  p->s2r_grid = sms * p->occ[2];
+  p->s2b_grid = sms * p->occ[3];
   // level tables of the reduce warps (zero between tiles)
   const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
   if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
@@ -266,7 +277,7 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[2], s);
   sj::launch_scan1(p->d_job, p->scan_blocks, s);
   if (ev) cudaEventRecord(ev[3], s);
-  sj::stage1_flatten_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  sj::stage1_flatten_kernel<<<p->fl_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
   sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
@@ -493,6 +504,95 @@ extern "C" sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n) {
 
 extern "C" int sj_parser_kernels_per_run(const sj_parser *p) {
   return p ? (int)kernels_per_run(p) : 0;
+}
+
+// ---- launch shapes and their autotuner ----------------------------------
+static void drop_graphs(sj_parser *p) {
+  for (cudaGraphExec_t &g : p->graphs)
+    if (g) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+}
+
+extern "C" sj_status sj_parser_get_launch(const sj_parser *p, uint32_t *blocks_per_sm,
+                                          uint32_t *max_blocks_per_sm) {
+  if (!p || !blocks_per_sm) return SJ_INVALID_ARG;
+  const int g[4] = {p->s1_grid, p->fl_grid, p->s2r_grid, p->s2b_grid};
+  for (int k = 0; k < 4; k++) {
+    blocks_per_sm[k] = (uint32_t)(g[k] / p->sms);
+    if (max_blocks_per_sm) max_blocks_per_sm[k] = (uint32_t)p->occ[k];
+  }
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parser_set_launch(sj_parser *p, const uint32_t *blocks_per_sm) {
+  if (!p || !blocks_per_sm) return SJ_INVALID_ARG;
+  for (int k = 0; k < 4; k++)
+    if (blocks_per_sm[k] < 1 || (int)blocks_per_sm[k] > p->occ[k]) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  p->s1_grid = p->sms * (int)blocks_per_sm[0];
+  p->fl_grid = p->sms * (int)blocks_per_sm[1];
+  p->s2r_grid = p->sms * (int)blocks_per_sm[2];  // the reduce level tables fit the largest grid
+  p->s2b_grid = p->sms * (int)blocks_per_sm[3];
+  drop_graphs(p);
+  return SJ_SUCCESS;
+}
+
+// For each of the four main kernels in turn, try every resident-block count
+// per SM its occupancy allows (the others fixed at their current choice),
+// time the kernel with events over `reps` parses of the sample, and keep the
+// fastest.  The stages of a run do not share launch shapes, so the kernels
+// are tuned one at a time.
+extern "C" sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len,
+                                        void *stream, int reps, uint32_t *blocks_per_sm,
+                                        float *best_ms) {
+  if (!p || (!bytes && len) || reps < 1) return SJ_INVALID_ARG;
+  if (len > p->max_bytes) return SJ_CAPACITY;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  const bool was_profiling = p->profiling;
+  p->profiling = true;
+  static const int stage_of[4] = {1, 3, 4, 6};  // index into the 8 stage times
+  uint32_t cur[4];
+  sj_parser_get_launch(p, cur, nullptr);
+  float best[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; k++) {
+    uint32_t pick = cur[k];
+    float pick_ms = 3.4e38f;
+    for (int b = 1; b <= p->occ[k]; b++) {
+      uint32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
+      trial[k] = (uint32_t)b;
+      if ((r = sj_parser_set_launch(p, trial))) break;
+      float sum = 0;
+      for (int i = 0; i <= reps; i++) {  // the first run warms up
+        if ((r = sj_parse_async(p, bytes, len, stream))) break;
+        float ms[sj_parser::kStages];
+        if ((r = sj_parser_stage_times(p, ms, sj_parser::kStages))) break;
+        if (i) sum += ms[stage_of[k]];
+      }
+      if (r) break;
+      const float avg = sum / (float)reps;
+      if (avg < pick_ms) {
+        pick_ms = avg;
+        pick = (uint32_t)b;
+      }
+    }
+    if (r) break;
+    cur[k] = pick;
+    best[k] = pick_ms;
+  }
+  wait_pending(p);
+  p->profiling = was_profiling;
+  const int r2 = sj_parser_set_launch(p, cur);
+  if (r) return r;
+  if (r2) return r2;
+  if (blocks_per_sm)
+    for (int k = 0; k < 4; k++) blocks_per_sm[k] = cur[k];
+  if (best_ms)
+    for (int k = 0; k < 4; k++) best_ms[k] = best[k];
+  return SJ_SUCCESS;
 }
 
 extern "C" const char *sj_error_name(int code) {
