@@ -377,6 +377,46 @@ def batch_leg(args, dev) -> dict:
     }
 
 
+def query_leg(args, dev) -> dict:
+    """The paper's tape query (Table "tab:userid"): parse a twitter-like
+    document and select the distinct user.id values from its device tape."""
+    import torch
+
+    import gen
+    import paper_1902_08318_gb300 as sj
+    doc = gen.tweets(4100, 256 << 20, 200_000)
+    B = int(doc.size)
+    d = torch.from_numpy(np.require(doc, requirements=["W"])).to(dev)
+    p = sj.Parser(max_bytes=B + 64)
+    q = sj.Query(1 << 20)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        r = p.parse(d, stream=stream)
+        vals = q.distinct(r, ("user", "id"), stream=stream)
+    torch.cuda.synchronize()
+    k = max(3, min(args.steps, 10))
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+    t_parse = t_query = 0.0
+    for _ in range(k):
+        ev[0].record(stream)
+        r = p.parse(d, stream=stream)
+        ev[1].record(stream)
+        vals = q.distinct(r, ("user", "id"), stream=stream)
+        ev[2].record(stream)
+        torch.cuda.synchronize()
+        t_parse += ev[0].elapsed_time(ev[1])
+        t_query += ev[1].elapsed_time(ev[2])
+    t_parse /= k
+    t_query /= k
+    return {"workload": f"twitter-like document ({B} bytes, statuses with nested user objects, "
+                        "200,000 user ids), distinct user.id",
+            "distinct_values": int(vals.numel()),
+            "parse_GB_per_s": round(B / (t_parse * 1e-3) / 1e9, 2),
+            "query_GB_per_s": round(B / (t_query * 1e-3) / 1e9, 2),
+            "parse_and_query_GB_per_s": round(B / ((t_parse + t_query) * 1e-3) / 1e9, 2),
+            "ms_parse": round(t_parse, 4), "ms_query": round(t_query, 4), "steps": k}
+
+
 def serving_leg(args) -> dict:
     """Serving (config4): the arrival trace replayed natively against the
     continuous-batching server (latency = result seen minus arrival)."""
@@ -427,8 +467,57 @@ def cpu_baseline(args) -> dict:
         sample = make_doc(args.workload, 1000 if args.workload == "config1" else 0).tobytes()
         what = f"the whole {args.workload} document ({len(sample)} bytes), single-threaded"
     gbs, dt = oracle_gbs(sample)
-    return {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": what, "seconds": round(dt, 2), "host_cores": os.cpu_count()}
+    out = {"value": round(gbs, 4), "unit": "GB/s", "cores": 1, "kind": "oracle",
+           "sample": what, "seconds": round(dt, 2), "host_cores": os.cpu_count()}
+    if not args.no_batch:
+        out["batch"] = oracle_batch()
+    return out
+
+
+def _oracle_errors(args):
+    """Worker: the oracle over documents [a, b) of a batch held in shared memory."""
+    from multiprocessing import shared_memory
+
+    import oracle
+    name, size, off, a, b = args
+    shm = shared_memory.SharedMemory(name=name)
+    try:
+        buf = np.ndarray((size,), dtype=np.uint8, buffer=shm.buf)
+        lo, hi = int(off[a]), int(off[b])
+        errs = oracle.parse_many_errors(buf[lo:hi], off[a: b + 1] - off[a])
+        del buf
+        return int(np.count_nonzero(errs))
+    finally:
+        shm.close()
+
+
+def oracle_batch() -> dict:
+    """The oracle over the whole config3 batch, one worker process per host
+    core (the batch in shared memory; only the parse is timed)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+
+    import gen
+    buf, off = gen.config3()
+    n = off.size - 1
+    workers = os.cpu_count() or 1
+    shm = shared_memory.SharedMemory(create=True, size=int(buf.size))
+    try:
+        np.ndarray((buf.size,), dtype=np.uint8, buffer=shm.buf)[:] = buf
+        cuts = np.linspace(0, n, workers + 1).astype(np.int64)
+        jobs = [(shm.name, int(buf.size), off, int(a), int(b)) for a, b in zip(cuts[:-1], cuts[1:])]
+        with mp.get_context("spawn").Pool(workers) as pool:
+            pool.map(_oracle_errors, [(shm.name, int(buf.size), off, 0, 1)] * workers)  # start-up
+            t0 = time.perf_counter()
+            bad = sum(pool.map(_oracle_errors, jobs))
+            dt = time.perf_counter() - t0
+    finally:
+        shm.close()
+        shm.unlink()
+    return {"docs_per_s": round(n / dt, 1), "GB_per_s": round(int(off[-1]) / dt / 1e9, 3),
+            "cores": workers, "kind": "oracle", "invalid_docs": bad,
+            "sample": f"all {n} documents of config3 ({int(off[-1])} bytes), one process per core",
+            "seconds": round(dt, 3)}
 
 
 def run_reference(args, rank: int) -> dict | None:
@@ -479,6 +568,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the end-to-end leg (profiling runs)")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config3) leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-query", action="store_true", help="skip the tape-query leg")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (config4) leg")
     ap.add_argument("--doc-mb", type=int, default=0,
                     help="config2 document size in MiB (default 1024; smaller for ncu captures)")
@@ -510,6 +600,8 @@ def main():
         dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
         if not args.no_batch:
             out["batch"] = batch_leg(args, dev)
+        if not args.no_query:
+            out["query"] = query_leg(args, dev)
         if not args.no_serving:
             out["serving"] = serving_leg(args)
         if not args.no_cpu_baseline:

@@ -65,6 +65,9 @@ def _load():
                                     ctypes.c_void_p, ctypes.c_uint64]
         lib.sjg_geo.restype = ctypes.c_uint64
         lib.sjg_geo.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_uint64]
+        lib.sjg_tweets.restype = ctypes.c_uint64
+        lib.sjg_tweets.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64,
+                                   ctypes.c_void_p, ctypes.c_uint64]
         lib.sjg_strings.restype = ctypes.c_uint64
         lib.sjg_strings.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_void_p,
                                     ctypes.c_uint64]
@@ -99,6 +102,13 @@ def geo(seed: int, target: int = 2_500_000) -> np.ndarray:
 def strings_heavy(seed: int, target: int) -> np.ndarray:
     lib = _load()
     return _call(lambda *a: lib.sjg_strings(seed, target, *a), target)
+
+
+def tweets(seed: int, target: int = 631_514, n_users: int = 2000) -> np.ndarray:
+    """Twitter-like document (statuses with nested user objects): the stand-in
+    for twitter.json in the user.id query of Table "tab:userid"."""
+    lib = _load()
+    return _call(lambda *a: lib.sjg_tweets(seed, target, n_users, *a), target)
 
 
 def config0(seed: int = 0) -> np.ndarray:

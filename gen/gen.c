@@ -380,3 +380,84 @@ uint64_t sjg_strings(uint64_t seed, uint64_t target, uint8_t *out, uint64_t cap)
   put(&w, ']');
   return w.overflow ? 0 : w.n;
 }
+
+/* ---- tweets: a stand-in for twitter.json (the paper's user.id query,
+ * Table "tab:userid"): {"statuses": [tweet, ...], "search_metadata": {...}}.
+ * Each tweet carries "id", "text", "user": {"id", "name", "screen_name",
+ * "followers_count", ...}, counters, "entities" and, for 1 in 8, a
+ * "retweeted_status" with its own "user".  User ids come from a pool of
+ * n_users values, so the distinct count is below the number of users. */
+static void emit_uint_digits(wbuf *w, uint64_t v) {
+  char t[24];
+  int n = 0;
+  do { t[n++] = (char)('0' + v % 10); v /= 10; } while (v);
+  while (n) put(w, (uint8_t)t[--n]);
+}
+
+static void emit_text(wbuf *w, rng_t *r, const recopt *o, int lo, int hi) {
+  recopt t = *o;
+  t.str_min = lo;
+  t.str_max = hi;
+  t.long_string_p = 0;
+  t.straddle_p = 0;
+  emit_string(w, r, &t);
+}
+
+static void emit_user(wbuf *w, rng_t *r, const recopt *o, const uint64_t *pool, uint64_t n_users) {
+  const uint64_t id = pool[rbelow(r, n_users)];
+  puts_(w, "{\"id\":"); emit_uint_digits(w, id);
+  puts_(w, ",\"id_str\":\""); emit_uint_digits(w, id); put(w, '"');
+  puts_(w, ",\"name\":"); emit_text(w, r, o, 3, 20);
+  puts_(w, ",\"screen_name\":"); emit_key(w, r);
+  puts_(w, ",\"location\":"); emit_text(w, r, o, 0, 24);
+  puts_(w, ",\"description\":"); emit_text(w, r, o, 0, 120);
+  puts_(w, ",\"followers_count\":"); emit_uint_digits(w, rbelow(r, 2000000));
+  puts_(w, ",\"friends_count\":"); emit_uint_digits(w, rbelow(r, 5000));
+  puts_(w, ",\"verified\":"); puts_(w, rbelow(r, 10) ? "false" : "true");
+  puts_(w, ",\"profile_image_url\":null}");
+}
+
+static void emit_tweet(wbuf *w, rng_t *r, const recopt *o, const uint64_t *pool, uint64_t n_users,
+                       int nested) {
+  puts_(w, "{\"created_at\":"); emit_text(w, r, o, 30, 30);
+  puts_(w, ",\"id\":"); emit_uint_digits(w, 500000000000000000ull + rbelow(r, 400000000000000000ull));
+  puts_(w, ",\"text\":"); emit_text(w, r, o, 20, 140);
+  puts_(w, ",\"user\":"); emit_user(w, r, o, pool, n_users);
+  puts_(w, ",\"retweet_count\":"); emit_uint_digits(w, rbelow(r, 10000));
+  puts_(w, ",\"favorite_count\":"); emit_uint_digits(w, rbelow(r, 10000));
+  puts_(w, ",\"entities\":{\"hashtags\":[");
+  const int nh = (int)rbelow(r, 3);
+  for (int i = 0; i < nh; i++) {
+    if (i) put(w, ',');
+    puts_(w, "{\"text\":"); emit_key(w, r); puts_(w, ",\"indices\":[");
+    emit_uint_digits(w, rbelow(r, 100)); put(w, ','); emit_uint_digits(w, rbelow(r, 140));
+    puts_(w, "]}");
+  }
+  puts_(w, "],\"urls\":[]}");
+  puts_(w, ",\"favorited\":false,\"lang\":\"en\"");
+  if (!nested && rbelow(r, 8) == 0) {
+    puts_(w, ",\"retweeted_status\":");
+    emit_tweet(w, r, o, pool, n_users, 1);
+  }
+  put(w, '}');
+}
+
+uint64_t sjg_tweets(uint64_t seed, uint64_t target, uint64_t n_users, uint8_t *out, uint64_t cap) {
+  rng_t r = {seed * 0x9E3779B97F4A7C15ull + 7};
+  wbuf w = {out, 0, cap, 0};
+  recopt o;
+  init_opts(&o, 0, 0.03);
+  if (n_users == 0) n_users = 1;
+  if (n_users > 1000000) n_users = 1000000;
+  static uint64_t pool[1000000];
+  for (uint64_t i = 0; i < n_users; i++) pool[i] = 1000 + rbelow(&r, 4000000000ull);
+  puts_(&w, "{\"statuses\":[");
+  int first = 1;
+  while (w.n + 8 < target) {
+    if (!first) put(&w, ',');
+    first = 0;
+    emit_tweet(&w, &r, &o, pool, n_users, 0);
+  }
+  puts_(&w, "],\"search_metadata\":{\"count\":100,\"max_id\":null}}");
+  return w.overflow ? 0 : w.n;
+}

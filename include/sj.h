@@ -259,6 +259,25 @@ sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len, v
 sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t len, uint32_t *d_indices,
                                     uint32_t *d_result, void *stream);
 
+/* ---- Tape query ------------------------------------------------------------
+ * Distinct integer values at a key path, e.g. {"user", "id"} -- the paper's
+ * example query over a parsed document (Sec. 4.5, Table "tab:userid").  The
+ * path may start at any object of the document; a value counts when every key
+ * but the last names an object and the last names an int64 ('l').  The tape
+ * and strings are a document's device outputs of a successful parse
+ * (tape_words, string_bytes from its result); any other tape is read without
+ * faults but gives no meaningful answer.  A query object owns a device hash
+ * set for up to max_values distinct values (SJ_CAPACITY beyond).  The
+ * values, in no particular order, stay in device memory owned by the query
+ * until its next call.  Synchronous on `stream`. */
+typedef struct sj_query sj_query;
+sj_status sj_query_create(sj_query **out, uint64_t max_values);
+void sj_query_destroy(sj_query *q);
+sj_status sj_query_distinct(sj_query *q, const uint64_t *d_tape, uint64_t tape_words,
+                            const uint8_t *d_strings, uint64_t string_bytes,
+                            const char *const *path, uint32_t path_len, void *stream,
+                            uint64_t *n_values, const uint64_t **d_values);
+
 /* Name of an sj_error code ("SUCCESS", "TAPE_ERROR", ...). */
 const char *sj_error_name(int code);
 

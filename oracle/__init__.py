@@ -167,3 +167,35 @@ def parse_many_errors(buf: np.ndarray, offsets: np.ndarray, max_depth: int = 0) 
     err = np.zeros(max(n, 0), dtype=np.int32)
     _load().sjo_parse_many_errors(b.ctypes.data, off.ctypes.data, n, max_depth, err.ctypes.data)
     return err
+
+
+def distinct_path_values(doc: bytes, path) -> set:
+    """The tape query of Sec. 4.5 / Table "tab:userid" written out: every
+    object of the document (at any depth) whose keys path[0], ..., path[-2]
+    name nested objects and whose path[-1] names an integer contributes that
+    integer; returns the set of them.  A plain recursive walk over Python's
+    json decoder (a library routine standing for the parse)."""
+    import json
+    out = set()
+
+    def at_path(o):
+        for k in path[:-1]:
+            if not isinstance(o, dict) or not isinstance(o.get(k), dict):
+                return None
+            o = o[k]
+        v = o.get(path[-1]) if isinstance(o, dict) else None
+        return v if isinstance(v, int) and not isinstance(v, bool) else None
+
+    def walk(x):
+        if isinstance(x, dict):
+            v = at_path(x)
+            if v is not None:
+                out.add(v)
+            for y in x.values():
+                walk(y)
+        elif isinstance(x, list):
+            for y in x:
+                walk(y)
+
+    walk(json.loads(doc))
+    return out

@@ -25,7 +25,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsj.so")
-_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu", "server.cpp"]
+_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu", "server.cpp",
+            "query.cu"]
 _HEADERS = ["sj_internal.cuh", "s1_common.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
@@ -150,6 +151,13 @@ def load(path: str | None = None):
     lib.sj_parse_batch_wait.argtypes = [vp, vp, ctypes.POINTER(vp), ctypes.POINTER(vp),
                                         ctypes.POINTER(vp)]
     lib.sj_parse_batch_wait.restype = ctypes.c_int
+    lib.sj_query_create.argtypes = [ctypes.POINTER(vp), u64]
+    lib.sj_query_create.restype = ctypes.c_int
+    lib.sj_query_destroy.argtypes = [vp]
+    lib.sj_query_destroy.restype = None
+    lib.sj_query_distinct.argtypes = [vp, vp, u64, vp, u64, vp, u32, vp, ctypes.POINTER(u64),
+                                      ctypes.POINTER(vp)]
+    lib.sj_query_distinct.restype = ctypes.c_int
     lib.sj_parser_get_launch.argtypes = [vp, vp, vp]
     lib.sj_parser_get_launch.restype = ctypes.c_int
     lib.sj_parser_set_launch.argtypes = [vp, vp]
@@ -187,7 +195,8 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_parse_batch_wait", "sj_parser_device_bytes", "sj_server_create",
             "sj_server_destroy", "sj_server_slots", "sj_server_device_bytes", "sj_server_batches",
             "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay",
-            "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune"]
+            "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune",
+            "sj_query_create", "sj_query_destroy", "sj_query_distinct"]
 TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
           "s2_build", "finalize")
@@ -441,3 +450,38 @@ class Server:
                                           arr.ctypes.data, n, lat.ctypes.data,
                                           ctypes.byref(wall)))
         return lat, wall.value
+
+
+class Query:
+    """Distinct int64 values at a key path over a parsed document's device
+    tape (sj_query_* of include/sj.h): the paper's user.id query."""
+
+    def __init__(self, max_values: int = 1 << 20):
+        self._lib = load()
+        h = ctypes.c_void_p()
+        _check(self._lib.sj_query_create(ctypes.byref(h), int(max_values)))
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.sj_query_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def distinct(self, result, path, stream=None):
+        """result: a successful Result of Parser.parse; path: e.g. ("user", "id").
+        Returns a device tensor (int64) of the distinct values."""
+        keys = [k.encode() for k in path]
+        arr = (ctypes.c_char_p * len(keys))(*keys)
+        n = ctypes.c_uint64()
+        vals = ctypes.c_void_p()
+        _check(self._lib.sj_query_distinct(self._h, result._p[1], result.tape_words,
+                                           result._p[2], result.string_bytes, arr, len(keys),
+                                           _stream_handle(stream), ctypes.byref(n),
+                                           ctypes.byref(vals)))
+        return _device_tensor(vals.value, n.value, "<i8")
