@@ -280,7 +280,7 @@ def report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_s
     algo_path = B + 4 * S + 8 * T + SB
     # algorithmic bytes of each kernel: what it must read or write at minimum
     algo = {"setup": 0, "s1_blocks": B, "s1_scan": 0, "s1_flatten": 4 * S,
-            "s2_reduce": 4 * S + lex, "s2_scan_frontier": 0,
+            "s2_reduce": 4 * S + lex, "s2_scan_frontier": 0, "s2_numbers": 0,
             "s2_build": 4 * S + lex + 8 * T + SB, "finalize": 0}
     dom = max(stage_ms, key=lambda k: stage_ms[k])
     achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9

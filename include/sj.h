@@ -216,9 +216,10 @@ sj_status sj_server_replay(sj_server *s, const uint8_t *bytes, const uint64_t *o
 /* Per-kernel timing.  With profiling on, runs launch their kernels directly
  * (not through the captured graph) with CUDA events recorded between them on
  * the caller's stream.  sj_parser_stage_times waits for the last run and
- * writes, in milliseconds, the durations of its 8 stages to ms[0..7]: setup,
+ * writes, in milliseconds, the durations of its 9 stages to ms[0..8]: setup,
  * stage-1 blocks, stage-1 tile scan, stage-1 flatten, stage-2 reduce, stage-2
- * tile scan and frontier, stage-2 build, finalize.  n must be at least 8. */
+ * tile scan and frontier, stage-2 numbers, stage-2 build, finalize.  n must be
+ * at least 9. */
 sj_status sj_parser_set_profiling(sj_parser *p, int enable);
 sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
 

@@ -199,7 +199,7 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_query_create", "sj_query_destroy", "sj_query_distinct"]
 TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
-          "s2_build", "finalize")
+          "s2_numbers", "s2_build", "finalize")
 
 
 class SJError(RuntimeError):

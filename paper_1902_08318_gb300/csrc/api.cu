@@ -20,6 +20,7 @@ __global__ void stage1_blocks_kernel(const Job *job);
 __global__ void stage1_flatten_kernel(const Job *job);
 __global__ void stage2_reduce_kernel(const Job *job);
 __global__ void stage2_build_kernel(const Job *job);
+__global__ void numbers_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
 __global__ void spt_build_kernel(const Job *job, uint32_t src);
 __global__ void jump_kernel(const Job *job);
@@ -58,6 +59,9 @@ struct sj_parser {
   uint64_t *d_meta = nullptr;
   uint16_t *d_open_g = nullptr;
   uint8_t *d_unesc = nullptr;
+  uint64_t *d_numv = nullptr;
+  uint32_t *d_nlist = nullptr;
+  uint32_t *d_tile_nnum = nullptr;
   uint64_t *d_front = nullptr;
   uint32_t *d_surv = nullptr;
   uint32_t *d_idx = nullptr;
@@ -76,6 +80,7 @@ struct sj_parser {
   sj_doc_result *h_results = nullptr;
   // launch shapes
   int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
+  int num_grid = 0;
   int sms = 0;
   int occ[4] = {1, 1, 1, 1};  // most resident blocks per SM: s1 blocks, flatten, reduce, build
   uint32_t scan_blocks = 0, spt_levels = 0;
@@ -85,7 +90,7 @@ struct sj_parser {
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graphs[kBuckets] = {};
   cudaEvent_t done = nullptr;
-  static constexpr int kStages = 8;
+  static constexpr int kStages = 9;
   cudaEvent_t prof[kStages + 1] = {};
   bool profiling = false;
   bool profiled_run = false;
@@ -126,7 +131,7 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
                  p->d_scan_agg, p->d_scan_pre, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
                  p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
-                 p->d_open_g, p->d_unesc};
+                 p->d_open_g, p->d_unesc, p->d_numv, p->d_nlist, p->d_tile_nnum};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_job) cudaFreeHost(p->h_job);
@@ -164,6 +169,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_unesc, max_bytes + 64))) return r;
+  if ((r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_nlist, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_tile_nnum, tiles))) return r;
   if ((r = dalloc(p, &p->d_front, max_bytes + tiles + 16))) return r;
   if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_idx, max_bytes + 16))) return r;
@@ -208,6 +216,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
   if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
   CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
+  int occn = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, sj::numbers_kernel, 128, 0));
+  p->num_grid = sms * (occn > 0 ? occn : 1);
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
 
@@ -235,6 +246,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.meta = p->d_meta;
   J.open_g = p->d_open_g;
   J.unesc = p->d_unesc;
+  J.numv = p->d_numv;
+  J.nlist = p->d_nlist;
+  J.tile_nnum = p->d_tile_nnum;
   J.front = p->d_front;
   J.surv = p->d_surv;
   J.idx = p->d_idx;
@@ -287,15 +301,18 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
-  sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::numbers_kernel<<<p->num_grid, 128, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[7], s);
-  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);
+  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[9], s);
 }
 
 static uint32_t kernels_per_run(const sj_parser *p) {
   return 2 /* setup, blocks */ + 3 + 1 /* scan1, flatten */ + 1 + 3 /* reduce, scan2 */ +
-         (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 + 1 /* build, finalize */;
+         (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 /* numbers */ +
+         1 + 1 /* build, finalize */;
 }
 
 // The launch sequence of one run, captured once per bucket of document
@@ -554,7 +571,7 @@ extern "C" sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint
   if ((r = wait_pending(p))) return r;
   const bool was_profiling = p->profiling;
   p->profiling = true;
-  static const int stage_of[4] = {1, 3, 4, 6};  // index into the 8 stage times
+  static const int stage_of[4] = {1, 3, 4, 7};  // index into the stage times
   uint32_t cur[4];
   sj_parser_get_launch(p, cur, nullptr);
   float best[4] = {0, 0, 0, 0};

@@ -33,10 +33,11 @@ constexpr int kS2Warps = kS2Threads / 32;
 constexpr int kHalo = 1024;                    // staged bytes past the tile's end
 constexpr int kStageBytes = kTileBytes + kHalo;
 constexpr int kStageBytesR = kTileBytes + 512;  // the reduce pass stages a shorter halo
+constexpr int kStageBytesB = kTileBytes + 512;  // and so does the build pass
 constexpr int kStageBlocksR = kStageBytesR / kBlockBytes;
 constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
 constexpr int kOpenSmem = 512;                 // levels kept in shared memory (mod 512)
-constexpr int kStrStage = 3328;                // string output of 32 strings, staged
+constexpr int kStrStage = 2816;                // string output of 32 strings, staged
 constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
 constexpr uint32_t kFrontSmem = 64;            // frontier slots of a tile kept in shared memory
 
@@ -262,7 +263,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     const uint32_t tt = t - j_min;
     const uint32_t nidx = J.doc_nidx[d];
     if ((J.doc_flags[d] & kDocBad) || nidx == 0) {
-      if (lane == 0) J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
+      if (lane == 0) {
+        J.s2_rec[t] = S2Agg{0, 0, 0, tt == 0, 0};
+        J.tile_nnum[t] = 0;
+      }
       continue;
     }
     if (lane == 0) J.s2_rec[t].s = 0;  // walks add to it, from this tile on
@@ -288,6 +292,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
                                                    : OpenTable{open_g, 0xFFFFFFFFu, kLevelOff};
     uint64_t sb = 0;  // string-buffer bytes of this lane's strings without escapes
     uint32_t shead = 0, stail = 0;
+    uint32_t nnum = 0;  // number tokens of the tile so far (listed for numbers_kernel)
     // strings: the next 32 queued get their length from the masks; those the
     // masks cannot decide go to the walk queue
     auto flush_strings = [&]() {
@@ -358,6 +363,11 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
         mx = max(mx, max(E, D));
       }
       enqueue(W.sq, stail, valid && kind == K_STRING, RQEntry{pos, nxt, j}, lane);
+      {
+        const unsigned nb = __ballot_sync(0xFFFFFFFFu, valid && kind == K_NUMBER);
+        if (valid && kind == K_NUMBER) J.nlist[ib + off + nnum + __popc(nb & ((1u << lane) - 1u))] = off + j;
+        nnum += __popc(nb);
+      }
       const uint32_t tot = __shfl_sync(0xFFFFFFFFu, vi, 31);
       depth += (int32_t)(tot & 0xFFu) - 32;
       tape += tot >> 8;
@@ -387,6 +397,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     for (int32_t v = max(mn, -kLevelOff) + lane; v <= min(mx, kLevelOff); v += 32) ot.at(v) = 0;
     __syncwarp();
     if (lane == 0) {
+      J.tile_nnum[t] = nnum;
       S2Agg &a = J.s2_rec[t];
       a.dd = depth;
       a.mn = mn;
@@ -399,17 +410,70 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
 }
 
 // ---------------------------------------------------------------------------
+// Numbers (Sec. 3.2.1): one warp per tile, one lane per number token listed
+// by the reduce pass.  Each lane copies its lexeme and the byte after it
+// (at most kNumWindow bytes, in 16-byte chunks) into shared memory and
+// converts it there; longer lexemes are read in place.  The value goes to
+// `numv`, the tag ('l' or 'd') or the error code to the token's `slen` entry.
+constexpr int kNumWindow = 48;
+constexpr int kNumThreads = 128;
+__global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restrict__ job) {
+  const Job &J = *job;
+  __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
+  const int lane = threadIdx.x & 31;
+  uint8_t *my = win[threadIdx.x];
+  const uint32_t n_tiles = J.counters[2];
+  const uint32_t warps = gridDim.x * (kNumThreads / 32);
+  for (uint32_t t = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const uint32_t d = doc_of_tile(J, t);
+    const uint32_t nidx = J.doc_nidx[d];
+    if ((J.doc_flags[d] & kDocBad) || nidx == 0) continue;
+    const uint32_t m = J.tile_nnum[t];
+    if (m == 0) continue;
+    const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
+    const uint8_t *doc = J.base + J.doc_off[d];
+    const uint64_t ib = idx_base(J, d);
+    const uint32_t off = J.tile_off[t];
+    for (uint32_t k = lane; k < m; k += 32) {
+      const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
+      const uint64_t pos = J.idx[ib + rel];
+      const uint64_t nxt = rel + 1 < nidx ? J.idx[ib + rel + 1] : len;
+      const uint64_t wend = min(len, pos + kNumWindow);
+      uint8_t tag = 0;
+      uint64_t v = 0;
+      int nc;
+      if (nxt < wend || (nxt == len && len <= wend)) {  // lexeme and terminator fit the window
+        const uintptr_t g0 = (uintptr_t)(doc + pos), a0 = g0 & ~(uintptr_t)15;
+        const uintptr_t gend = (uintptr_t)(doc + wend);
+        for (uintptr_t c = a0; c < gend; c += 16)
+          *reinterpret_cast<uint4 *>(my + (c - a0)) = __ldg(reinterpret_cast<const uint4 *>(c));
+        const uint8_t *sp = my + (g0 - a0);
+        nc = parse_number(sp, sp + (wend - pos), tag, v);
+      } else {
+        nc = parse_number(doc + pos, doc + len, tag, v);
+      }
+      if (nc) {
+        J.slen[ib + rel] = kSlenErr | (uint32_t)nc;
+      } else {
+        J.slen[ib + rel] = tag;
+        J.numv[ib + rel] = v;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
 // Stage-2 build: grammar, tape words, numbers and strings.
 // ---------------------------------------------------------------------------
 struct __align__(16) BuildSmem {
-  uint8_t bytes[kStageBytes + 64];
-  uint8_t ubytes[kStageBytes + 64];  // the same window of the scratch buffer (escaped strings)
+  uint8_t bytes[kStageBytesB + 64];
+  uint8_t ubytes[kStageBytesB + 64];  // the same window of the scratch buffer (escaped strings)
   uint8_t sout[kStrStage];  // the string-buffer bytes of 32 strings, before a coalesced copy
-  QEntry nq[kQueue];        // numbers awaiting conversion
   QEntry sq[kQueue];        // strings awaiting output
   uint64_t front[kFrontSmem];  // the first frontier slots of the tile
 };
-static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytes + 64) % 16 == 0,
+static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytesB + 64) % 16 == 0 &&
+                  kStrStage >= kStageBytesB + 5 * 32 + 16,
               "per-warp staging must stay 16-byte aligned");
 
 // Grammar (Sec. 3.2, RFC 8259): which previous tokens may precede a token of
@@ -444,7 +508,7 @@ __device__ __forceinline__ void put_string(uint8_t *__restrict__ o, uint32_t n,
   o[4 + n] = 0;
 }
 
-__global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__restrict__ job) {
+__global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ BuildSmem WS[kS2Warps];
   __shared__ uint16_t s_gram[32];
@@ -491,39 +555,14 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
     // starts inside, deepest first (levels d_start down to max(1, low))
     const uint32_t nfront = pre.d_start >= max(1, pre.low) ? (uint32_t)(pre.d_start - max(1, pre.low) + 1) : 0u;
     for (uint32_t k = lane; k < min(nfront, kFrontSmem); k += 32) W.front[k] = front[k];
-    const Staged sv = stage_tile(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
-    uint32_t nhead = 0, ntail = 0, shead = 0, stail = 0;
+    const Staged sv = stage_tile<kStageBytesB>(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
+    uint32_t shead = 0, stail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
     Staged us{};  // the scratch window, staged at the first string with escapes
     bool us_staged = false;
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
     // numbers (Sec. 3.2.1), 32 at a time
-    auto flush_numbers = [&]() {
-      const uint32_t m = min(32u, ntail - nhead);
-      if ((uint32_t)lane < m) {
-        const QEntry e = W.nq[(nhead + lane) & (kQueue - 1)];
-        uint8_t tag;
-        uint64_t v;
-        int nc;
-        const uint64_t q0 = e.pos, q1 = e.nxt;
-        if (q1 < sv.slimit || (q1 == len && len <= sv.slimit)) {  // lexeme and terminator staged
-          const uint8_t *sp = sv.smem + (q0 - sv.sbase);
-          nc = parse_number(sp, sp + (min(len, sv.slimit) - q0), tag, v);
-        } else {
-          nc = parse_number(doc + q0, doc + len, tag, v);
-        }
-        const uint64_t tp = (uint64_t)pre.tape_start + e.tp;
-        if (nc) {
-          report(J, d, (uint64_t)off + e.j, nc);
-        } else if (tp + 1 < tape_cap) {
-          tape[tp] = (uint64_t)tag << 56;
-          tape[tp + 1] = v;
-        }
-      }
-      nhead += m;
-      __syncwarp();
-    };
 
     // strings (Sec. 3.2.2), 32 at a time: their entries are contiguous in the
     // buffer, so they are built in shared memory and copied out coalesced
@@ -551,7 +590,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
       // Strings with escapes take their normalised bytes from the scratch
       // buffer of the reduce pass (same positions), staged once per tile.
       if (!us_staged && __any_sync(0xFFFFFFFFu, is_str && walk)) {
-        us = stage_tile(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
+        us = stage_tile<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
         us_staged = true;
       }
       const Staged &src = walk ? us : sv;
@@ -664,6 +703,13 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
             tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
             tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
           }
+        } else if (k == K_NUMBER) {  // converted by the reduce pass (Sec. 3.2.1)
+          if (sl_all & kSlenErr) {
+            if (!code) code = (int)(sl_all & 0xFFu);
+          } else if (tp + 1 < tape_cap) {
+            tape[tp] = (uint64_t)(sl_all & 0xFFu) << 56;
+            tape[tp + 1] = J.numv[ib + off + j];
+          }
         } else if (is_atom(k)) {
           const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
           const uint32_t nw = k == K_FALSE ? 5 : 4;
@@ -675,13 +721,10 @@ __global__ void __launch_bounds__(kS2Threads) stage2_build_kernel(const Job *__r
         }
         if (code) report(J, d, g, code);
       }
-      enqueue(W.nq, ntail, valid && k == K_NUMBER, QEntry{pos, nxt, j, trel, 0}, lane);
       enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel, sl}, lane);
       __syncwarp();
-      if (ntail - nhead >= 32) flush_numbers();
       if (stail - shead >= 32) flush_strings();
     }
-    while (nhead != ntail) flush_numbers();
     while (shead != stail) flush_strings();
     __syncwarp();  // every lane is done with this tile's staged bytes
   }
