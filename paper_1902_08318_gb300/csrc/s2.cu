@@ -630,6 +630,9 @@ __global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *
     // entry for every lane: a coalesced load, used only by strings)
     uint64_t meta_next = (uint32_t)lane < cnt ? J.meta[ib + off + lane] : 0ull;
     uint32_t sl_next = (uint32_t)lane < cnt ? J.slen[ib + off + lane] : 0u;
+    // a number's value word, loaded one chunk ahead once the kinds are known
+    uint64_t nv_next = ((uint32_t)lane < cnt && (meta_next & 15u) == K_NUMBER)
+                           ? J.numv[ib + off + lane] : 0ull;
     // kinds of the two tokens before the tile
     uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
     if (lane < 2 && off >= (uint32_t)lane + 1) {
@@ -645,6 +648,7 @@ __global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *
       ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
       const uint64_t meta = meta_next;
       const uint32_t sl_all = sl_next;
+      const uint64_t nv = nv_next;
       meta_next = j + 32 < cnt ? J.meta[ib + off + j + 32] : 0ull;
       sl_next = j + 32 < cnt ? J.slen[ib + off + j + 32] : 0u;
       const uint8_t k = (uint8_t)(meta & 15u);
@@ -708,7 +712,7 @@ __global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *
             if (!code) code = (int)(sl_all & 0xFFu);
           } else if (tp + 1 < tape_cap) {
             tape[tp] = (uint64_t)(sl_all & 0xFFu) << 56;
-            tape[tp + 1] = J.numv[ib + off + j];
+            tape[tp + 1] = nv;
           }
         } else if (is_atom(k)) {
           const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
@@ -722,6 +726,7 @@ __global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *
         if (code) report(J, d, g, code);
       }
       enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel, sl}, lane);
+      nv_next = (j + 32 < cnt && (meta_next & 15u) == K_NUMBER) ? J.numv[ib + off + j + 32] : 0ull;
       __syncwarp();
       if (stail - shead >= 32) flush_strings();
     }
