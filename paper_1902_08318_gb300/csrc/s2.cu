@@ -242,7 +242,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
       int err;
       // normalised bytes are never more than the raw ones: they stay within
       // the string's own span of the scratch buffer
-      const uint32_t n = string_walk<true>(sp, sp + e.n, err, J.unesc + (e.a - J.doc_off[0]));
+      const uint32_t n = string_walk8<true>(sp, sp + e.n, err, J.unesc + (e.a - J.doc_off[0]));
       uint64_t size;
       if (err) {
         J.slen[e.slot] = kSlenErr | (uint32_t)err;

@@ -141,3 +141,100 @@ __device__ __forceinline__ uint32_t string_walk(const uint8_t *s, const uint8_t 
 }
 
 }  // namespace sj
+
+namespace sj {
+
+// Bytes of an 8-byte window that are a quote, a backslash or below 0x20: bit
+// 7 of each byte, exact for the lowest flagged byte (a borrow can only flag
+// bytes above a flagged one).
+__device__ __forceinline__ uint32_t special_bits(uint32_t x) {
+  const uint32_t q = x ^ 0x22222222u, b = x ^ 0x5C5C5C5Cu;
+  return (((q - 0x01010101u) & ~q) | ((b - 0x01010101u) & ~b) | ((x - 0x20202020u) & ~x)) &
+         0x80808080u;
+}
+
+// string_walk with the same results (length, error, output bytes), shaped for
+// many strings walked side by side in one warp: every step copies the plain
+// bytes of an 8-byte window up to the first special byte and then handles at
+// most that one byte (end, error or one escape sequence), so lanes walking
+// different strings stay in step instead of splitting between a copy loop and
+// escape handling.
+template <bool WRITE>
+__device__ __forceinline__ uint32_t string_walk8(const uint8_t *s, const uint8_t *lim, int &err,
+                                                 uint8_t *out) {
+  uint32_t n = 0;
+  const uint8_t *p = s;
+  err = 0;
+  for (;;) {
+    if (p >= lim) { err = SJ_STRING_ERROR; return n; }
+    // window [p, p + 8): aligned words (a word holding a byte before lim lies
+    // in a page the document uses), bytes at or past lim forced to a quote
+    const uintptr_t ua = (uintptr_t)p;
+    const uint32_t *wp = reinterpret_cast<const uint32_t *>(ua & ~(uintptr_t)3);
+    const uint32_t sh = (uint32_t)(ua & 3) * 8;
+    const uint32_t w0 = wp[0];
+    const uint32_t w1 = reinterpret_cast<const uint8_t *>(wp + 1) < lim ? wp[1] : 0x22222222u;
+    const uint32_t w2 = reinterpret_cast<const uint8_t *>(wp + 2) < lim ? wp[2] : 0x22222222u;
+    uint32_t lo = __funnelshift_r(w0, w1, sh), hi = __funnelshift_r(w1, w2, sh);
+    const intptr_t avail = lim - p;
+    if (avail < 8) {
+      const uint64_t keep = (1ull << (8 * avail)) - 1;  // avail in [1, 7]
+      const uint64_t x = (((uint64_t)hi << 32) | lo) & keep;
+      const uint64_t y = x | (0x2222222222222222ull & ~keep);
+      lo = (uint32_t)y;
+      hi = (uint32_t)(y >> 32);
+    }
+    const uint32_t fl = special_bits(lo), fh = special_bits(hi);
+    const uint32_t k = fl ? (uint32_t)(__ffs(fl) - 1) >> 3 : (fh ? 4u + ((uint32_t)(__ffs(fh) - 1) >> 3) : 8u);
+    if (WRITE) {
+#pragma unroll
+      for (uint32_t i = 0; i < 8; i++)
+        if (i < k) out[n + i] = (uint8_t)((i < 4 ? lo >> (8 * i) : hi >> (8 * (i - 4))) & 0xFFu);
+    }
+    n += k;
+    p += k;
+    if (k == 8) continue;
+    if (p >= lim) { err = SJ_STRING_ERROR; return n; }
+    const uint32_t c = (k < 4 ? lo >> (8 * k) : hi >> (8 * (k - 4))) & 0xFFu;
+    if (c == '"') return n;
+    if (c != '\\') { err = SJ_UNESCAPED_CHARS; return n; }  // a byte below 0x20
+    if (p + 1 >= lim) { err = SJ_STRING_ERROR; return n; }
+    const uint32_t e = p[1];
+    if (e != 'u') {
+      uint32_t o;
+      switch (e) {
+        case '"': o = '"'; break;
+        case '\\': o = '\\'; break;
+        case '/': o = '/'; break;
+        case 'b': o = '\b'; break;
+        case 'f': o = '\f'; break;
+        case 'n': o = '\n'; break;
+        case 'r': o = '\r'; break;
+        case 't': o = '\t'; break;
+        default: err = SJ_STRING_ERROR; return n;
+      }
+      if (WRITE) out[n] = (uint8_t)o;
+      n++;
+      p += 2;
+      continue;
+    }
+    uint32_t cu;
+    if (!hex4(p + 2, lim, cu)) { err = SJ_STRING_ERROR; return n; }
+    p += 6;
+    if (cu >= 0xDC00 && cu <= 0xDFFF) { err = SJ_STRING_ERROR; return n; }
+    if (cu >= 0xD800 && cu <= 0xDBFF) {
+      uint32_t lo2;
+      if (p + 1 >= lim || p[0] != '\\' || p[1] != 'u' || !hex4(p + 2, lim, lo2) || lo2 < 0xDC00 ||
+          lo2 > 0xDFFF) {
+        err = SJ_STRING_ERROR;
+        return n;
+      }
+      p += 6;
+      cu = 0x10000 + ((cu - 0xD800) << 10) + (lo2 - 0xDC00);
+    }
+    if (WRITE) utf8_put(out + n, cu);
+    n += utf8_len(cu);
+  }
+}
+
+}  // namespace sj
