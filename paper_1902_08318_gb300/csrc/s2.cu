@@ -37,7 +37,8 @@ constexpr int kStageBytesB = kTileBytes + 512;  // and so does the build pass
 constexpr int kStageBlocksR = kStageBytesR / kBlockBytes;
 constexpr int kLevelOff = kMaxTileTokens;      // relative levels [-2048, 2048]
 constexpr int kOpenSmem = 512;                 // levels kept in shared memory (mod 512)
-constexpr int kStrStage = 2816;                // string output of 32 strings, staged
+constexpr int kStrStage = 2048;                // string output of 32 strings, staged (larger runs
+                                               // of strings are written directly)
 constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
 constexpr uint32_t kFrontSmem = 64;            // frontier slots of a tile kept in shared memory
 
@@ -114,11 +115,12 @@ __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc,
 // Position of the token after each token of a chunk (the next index, or the
 // document's end after its last token), with the next chunk prefetched.
 struct Positions {
-  uint32_t pos_next = 0;
+  uint32_t pos_next = 0, pos_next2 = 0;  // the next two chunks, loaded ahead
   uint32_t after = 0;  // (lane 0) the position after the tile's last token, loaded up front
   __device__ __forceinline__ void begin(const uint32_t *idxp, uint32_t off, uint32_t cnt,
                                         uint32_t nidx, uint64_t len, int lane) {
     pos_next = (uint32_t)lane < cnt ? idxp[off + lane] : 0u;
+    pos_next2 = (uint32_t)lane + 32 < cnt ? idxp[off + lane + 32] : 0u;
     if (lane == 0) after = off + cnt < nidx ? idxp[off + cnt] : (uint32_t)len;
   }
   __device__ __forceinline__ void next(uint32_t &pos, uint32_t &nxt, const uint32_t *idxp,
@@ -126,8 +128,9 @@ struct Positions {
                                        uint32_t base, int lane) {
     const uint32_t j = base + lane;
     pos = pos_next;
-    const uint32_t jn = j + 32;
-    pos_next = jn < cnt ? idxp[off + jn] : 0u;
+    pos_next = pos_next2;
+    const uint32_t jn = j + 64;
+    pos_next2 = jn < cnt ? idxp[off + jn] : 0u;
     uint32_t nx = __shfl_down_sync(0xFFFFFFFFu, pos, 1);
     const uint32_t first_next = __shfl_sync(0xFFFFFFFFu, pos_next, 0);
     const uint32_t aft = __shfl_sync(0xFFFFFFFFu, after, 0);
@@ -473,7 +476,7 @@ struct __align__(16) BuildSmem {
   uint64_t front[kFrontSmem];  // the first frontier slots of the tile
 };
 static_assert(sizeof(BuildSmem) % 16 == 0 && (kStageBytesB + 64) % 16 == 0 &&
-                  kStrStage >= kStageBytesB + 5 * 32 + 16,
+                  kStrStage % 16 == 0,
               "per-warp staging must stay 16-byte aligned");
 
 // Grammar (Sec. 3.2, RFC 8259): which previous tokens may precede a token of
@@ -508,7 +511,7 @@ __device__ __forceinline__ void put_string(uint8_t *__restrict__ o, uint32_t n,
   o[4 + n] = 0;
 }
 
-__global__ void __launch_bounds__(kS2Threads, 5) stage2_build_kernel(const Job *__restrict__ job) {
+__global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ BuildSmem WS[kS2Warps];
   __shared__ uint16_t s_gram[32];
