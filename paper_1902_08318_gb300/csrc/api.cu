@@ -363,6 +363,16 @@ static bool is_device_ptr(const void *ptr) {
   return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device's address of pinned (page-locked) host memory, or null.
+static const uint8_t *pinned_device_ptr(const void *ptr) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeHost ? static_cast<const uint8_t *>(a.devicePointer) : nullptr;
+}
+
 static int wait_pending(sj_parser *p) {
   if (!p->pending) return SJ_SUCCESS;
   p->pending = false;
@@ -375,12 +385,16 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
                   cudaStream_t stream) {
   int r;
   if ((r = wait_pending(p))) return r;
-  const uint8_t *base = bytes;
+  const uint8_t *base = bytes, *src = nullptr;
   if (!is_device_ptr(bytes)) {
-    CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
+    // one document in pinned host memory: stage 1 reads it over the host link
+    // and writes the device copy; otherwise copy it first
+    src = n_docs == 1 && total ? pinned_device_ptr(bytes) : nullptr;
+    if (!src) CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
     base = p->d_input;
   }
   p->h_job->base = base;
+  p->h_job->src = src;
   p->h_job->n_docs = n_docs;
   if (p->profiling) {
     // the same sequence as the graph, with events between the kernels

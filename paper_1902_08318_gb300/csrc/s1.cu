@@ -103,12 +103,29 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
-    const uint8_t *doc = J.base + J.doc_off[d];
+    // host input: read it over the host link here, once, and leave the device
+    // copy the later kernels read (the copy overlaps this kernel's work)
+    const uint8_t *doc = (J.src ? J.src : J.base) + J.doc_off[d];
     const uint64_t t0 = (uint64_t)tt * kTileBytes;
     const uint64_t blk = t0 + (uint64_t)lane * kBlockBytes;
 
     uint32_t w[16];
     load_block(doc, len, blk, w);
+    if (J.src && blk < len) {
+      uint8_t *dst = const_cast<uint8_t *>(J.base) + J.doc_off[d] + blk;
+      if (blk + kBlockBytes <= len && ((uintptr_t)dst & 15) == 0) {
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+          reinterpret_cast<uint4 *>(dst)[k] = make_uint4(w[4 * k], w[4 * k + 1], w[4 * k + 2], w[4 * k + 3]);
+      } else {
+        const uint32_t nb = (uint32_t)min((uint64_t)kBlockBytes, len - blk);
+#pragma unroll
+        for (int k = 0; k < 16; k++)
+#pragma unroll
+          for (int b = 0; b < 4; b++)
+            if ((uint32_t)(4 * k + b) < nb) dst[4 * k + b] = (uint8_t)(w[k] >> (8 * b));
+      }
+    }
     BlockMasks m;
     classify_block(w, m);
 

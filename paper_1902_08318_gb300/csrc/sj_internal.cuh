@@ -58,6 +58,8 @@ constexpr int kScanBlock = 1024;  // tiles per thread block in the tile scans
 // every call).
 struct Job {
   const uint8_t *base;      // 16-byte aligned buffer holding the documents
+  const uint8_t *src;       // when not null: the same bytes in pinned host memory; stage 1
+                            // reads them there and writes them to `base` (one document)
   const uint64_t *doc_off;  // n_docs + 1 byte offsets into base
   uint32_t n_docs;
   uint32_t max_depth;
