@@ -446,6 +446,95 @@ def serving_leg(args) -> dict:
     }
 
 
+def cost_model(args) -> dict:
+    """Per-stage time per input byte over a mix of synthetic documents (the
+    GPU analogue of the paper's Fig. "stacked"), the effect of minification
+    (Table "tab:minification"), and a least-squares refit of the paper's cost
+    model (Sec. 4.3): time = a*B + b*S + c*F + d over input bytes B,
+    structural indices S and floats F."""
+    import torch
+
+    import gen
+    import paper_1902_08318_gb300 as sj
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    mb = args.doc_mb or 64
+    docs = {}
+    for size in (mb << 18, mb << 20):  # a quarter and the whole size: fixed costs separate
+        tag = f" {size >> 20} MiB"
+        docs["records, pretty" + tag] = gen.records(1, size, root_array=True, pretty=True)
+        docs["records, minified" + tag] = gen.records(1, size, root_array=True, pretty=False)
+        docs["records, 30% non-ASCII, pretty" + tag] = gen.records(
+            2, size, root_array=True, pretty=True, nonascii_p=gen.NONASCII_P)
+        docs["records, 30% non-ASCII, minified" + tag] = gen.records(
+            2, size, root_array=True, pretty=False, nonascii_p=gen.NONASCII_P)
+        docs["config2-shaped (deep 1%)" + tag] = gen.config2(3, size=size)
+        docs["number-heavy (geo)" + tag] = gen.geo(4, size)
+        docs["string-heavy" + tag] = gen.strings_heavy(5, size)
+        docs["tweets" + tag] = gen.tweets(6, size, 100_000)
+    p = sj.Parser(max_bytes=max(int(d.size) for d in docs.values()) + 64)
+    p.set_profiling(True)
+    rows = []
+    for name, doc in docs.items():
+        d = torch.from_numpy(np.require(doc, requirements=["W"])).to(dev)
+        r = p.parse(d)
+        assert r.error == 0, (name, r.error_name)
+        tape = r.tape().cpu().numpy()
+        tags = (tape >> np.uint64(56)).astype(np.uint8)
+        is_val = np.concatenate([[False], (tags[:-1] != ord("l")) & (tags[:-1] != ord("d"))])
+        floats = int(np.count_nonzero((tags == ord("d")) & is_val))
+        ints = int(np.count_nonzero((tags == ord("l")) & is_val))
+        st = {k: 0.0 for k in sj.STAGES}
+        for _ in range(max(3, min(args.steps, 5))):
+            p.parse_async(d)
+            for k, v in p.stage_times().items():
+                st[k] += v
+        n = max(3, min(args.steps, 5))
+        st = {k: v / n for k, v in st.items()}
+        ms = sum(st.values())
+        B = int(doc.size)
+        rows.append({"doc": name, "B": B, "S": r.n_indices, "F": floats, "I": ints,
+                     "T": r.tape_words, "SB": r.string_bytes, "ms": round(ms, 4),
+                     "GB_per_s": round(B / ms / 1e6, 2),
+                     "ns_per_byte": {k: round(v * 1e6 / B, 5) for k, v in st.items()}})
+    y = np.array([r["ms"] * 1e6 for r in rows])  # ns
+
+    def fit(cols):
+        A = np.array([[r[c] for c in cols] + [1.0] for r in rows], dtype=np.float64)
+        try:  # non-negative coefficients (a cost per unit cannot be negative)
+            from scipy.optimize import nnls
+            coef, _ = nnls(A, y)
+        except ImportError:
+            coef, *_ = np.linalg.lstsq(A, y, rcond=None)
+        pred = A @ coef
+        r2 = 1.0 - float(((y - pred) ** 2).sum() / ((y - y.mean()) ** 2).sum())
+        return coef, r2
+
+    coef, r2 = fit(["B", "S", "F"])
+    coef_sb, r2_sb = fit(["B", "S", "F", "SB"])
+    # minification: the same kind of records with and without white space;
+    # compared per input byte and per tape word (the content parsed)
+    mini = {}
+    for base in ("records", "records, 30% non-ASCII"):
+        a = next(r for r in rows if r["doc"] == f"{base}, pretty {mb} MiB")
+        b = next(r for r in rows if r["doc"] == f"{base}, minified {mb} MiB")
+        mini[base] = {"pretty_ns_per_byte": round(a["ms"] * 1e6 / a["B"], 5),
+                      "minified_ns_per_byte": round(b["ms"] * 1e6 / b["B"], 5),
+                      "pretty_ns_per_tape_word": round(a["ms"] * 1e6 / a["T"], 4),
+                      "minified_ns_per_tape_word": round(b["ms"] * 1e6 / b["T"], 4),
+                      "bytes_per_tape_word": [round(a["B"] / a["T"], 2), round(b["B"] / b["T"], 2)]}
+    return {"mode": "cost-model", "documents": rows,
+            "fit_ns": {"per_byte": round(coef[0], 5), "per_index": round(coef[1], 4),
+                       "per_float": round(coef[2], 4), "fixed": round(coef[3], 1), "r2": round(r2, 4)},
+            "fit_ns_with_string_bytes": {"per_byte": round(coef_sb[0], 5),
+                                         "per_index": round(coef_sb[1], 4),
+                                         "per_float": round(coef_sb[2], 4),
+                                         "per_string_byte": round(coef_sb[3], 5),
+                                         "fixed": round(coef_sb[4], 1), "r2": round(r2_sb, 4)},
+            "minification": mini,
+            "note": "per-stage ns per input byte from CUDA events; one GB300; synthetic documents "
+                    f"of about {mb} MiB"}
+
+
 def oracle_gbs(sample: bytes, repeats: int = 1) -> tuple[float, float]:
     import oracle
     oracle.parse(sample[:1024])  # build + warm
@@ -569,6 +658,8 @@ def main():
     ap.add_argument("--no-batch", action="store_true", help="skip the batched (config3) leg")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
     ap.add_argument("--no-query", action="store_true", help="skip the tape-query leg")
+    ap.add_argument("--cost-model", action="store_true",
+                    help="per-stage breakdown, minification and cost-model fit (one JSON line)")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving (config4) leg")
     ap.add_argument("--doc-mb", type=int, default=0,
                     help="config2 document size in MiB (default 1024; smaller for ncu captures)")
@@ -592,6 +683,10 @@ def main():
     import __graft_entry__
     if rank == 0:
         __graft_entry__.build()
+    if args.cost_model:
+        if rank == 0:
+            print(json.dumps(cost_model(args)), flush=True)
+        return
     if dist:
         dist.barrier()
     out = run_ours(args, rank, world, dist)
