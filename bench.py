@@ -377,6 +377,36 @@ def batch_leg(args, dev) -> dict:
     }
 
 
+def small_doc_leg(args, dev) -> dict:
+    """The 2.5 MB number-heavy document (config1) and the 64 KB record document
+    (config0), parsed from HBM through sj_parse (the captured graph, waited
+    for): per-parse latency on the host clock, and the input bytes per second
+    that one parse after another achieves."""
+    import torch
+
+    import gen
+    import paper_1902_08318_gb300 as sj
+    out = {}
+    for name, doc in (("config1", gen.config1(1000)), ("config0", gen.config0(0))):
+        d = torch.from_numpy(np.require(doc, requirements=["W"])).to(dev)
+        p = sj.Parser(max_bytes=int(doc.size) + 64)
+        stream = torch.cuda.current_stream()
+        for _ in range(20):
+            r = p.parse(d, stream=stream)
+        assert r.error == 0, r.error_name
+        lat = []
+        for _ in range(300):
+            t0 = time.perf_counter()
+            p.parse(d, stream=stream)
+            lat.append(time.perf_counter() - t0)
+        out[name] = {"bytes": int(doc.size), "latency_ms_p50": round(pct(lat, 50) * 1e3, 4),
+                     "latency_ms_p99": round(pct(lat, 99) * 1e3, 4),
+                     "GB_per_s_at_p50": round(doc.size / pct(lat, 50) / 1e9, 2), "parses": len(lat),
+                     "kernels_per_parse": p.kernels_per_run()}
+    out["timing"] = "host clock around each synchronous sj_parse (graph launch, result header read back)"
+    return out
+
+
 def query_leg(args, dev) -> dict:
     """The paper's tape query (Table "tab:userid"): parse a twitter-like
     document and select the distinct user.id values from its device tape."""
@@ -697,6 +727,7 @@ def main():
             out["batch"] = batch_leg(args, dev)
         if not args.no_query:
             out["query"] = query_leg(args, dev)
+        out["small_docs"] = small_doc_leg(args, dev)
         if not args.no_serving:
             out["serving"] = serving_leg(args)
         if not args.no_cpu_baseline:

@@ -511,6 +511,35 @@ __device__ __forceinline__ void put_string(uint8_t *__restrict__ o, uint32_t n,
   o[4 + n] = 0;
 }
 
+// put_string for a staged entry: source and destination both in shared
+// memory, the source with at least 3 readable bytes past its end.  Bytes
+// until the destination is word aligned, then whole words (two aligned source
+// words and a funnel shift), then the tail.
+__device__ __forceinline__ void put_string_smem(uint8_t *__restrict__ o, uint32_t n,
+                                                const uint8_t *__restrict__ src) {
+  o[0] = (uint8_t)n; o[1] = (uint8_t)(n >> 8); o[2] = (uint8_t)(n >> 16); o[3] = (uint8_t)(n >> 24);
+  uint8_t *dst = o + 4;
+  uint32_t i = 0;
+  while (i < n && ((uintptr_t)(dst + i) & 3u)) {
+    dst[i] = src[i];
+    i++;
+  }
+  if (i + 4 <= n) {
+    const uintptr_t sa = (uintptr_t)(src + i);
+    const uint32_t *sw = reinterpret_cast<const uint32_t *>(sa & ~(uintptr_t)3);
+    const uint32_t sh = (uint32_t)(sa & 3u) * 8;
+    uint32_t lo = sw[0];
+    for (; i + 4 <= n; i += 4) {
+      const uint32_t hi = sw[1];
+      *reinterpret_cast<uint32_t *>(dst + i) = sh ? __funnelshift_r(lo, hi, sh) : lo;
+      lo = hi;
+      sw++;
+    }
+  }
+  for (; i < n; i++) dst[i] = src[i];
+  dst[n] = 0;
+}
+
 __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ BuildSmem WS[kS2Warps];
@@ -606,7 +635,7 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
         const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
         const uint64_t total = a + (so_hi - so_lo);
         if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (is_str) put_string(W.sout + a + (so - so_lo), (uint32_t)n, src.smem + (p0 - src.sbase));
+          if (is_str) put_string_smem(W.sout + a + (so - so_lo), (uint32_t)n, src.smem + (p0 - src.sbase));
           __syncwarp();
           uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
           const uint32_t units = (uint32_t)((total + 15) >> 4);
