@@ -413,34 +413,37 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
 }
 
 // ---------------------------------------------------------------------------
-// Numbers (Sec. 3.2.1): one warp per tile, one lane per number token listed
-// by the reduce pass.  Each lane copies its lexeme and the byte after it
-// (at most kNumWindow bytes, in 16-byte chunks) into shared memory and
-// converts it there; longer lexemes are read in place.  The value goes to
-// `numv`, the tag ('l' or 'd') or the error code to the token's `slen` entry.
+// Numbers (Sec. 3.2.1): each warp gathers the number tokens listed by the
+// reduce pass for its tiles into a queue and converts them 32 at a time, one
+// lane per number (a tile holds too few to fill a warp).  Each lane copies its
+// lexeme and the byte after it (at most kNumWindow bytes, in 16-byte chunks)
+// into shared memory and converts it there; longer lexemes are read in place.
+// The value goes to `numv`, the tag ('l' or 'd') or the error code to the
+// token's `slen` entry.
 constexpr int kNumWindow = 48;
 constexpr int kNumThreads = 128;
+struct NumEntry {
+  uint64_t slot;  // the token's index slot (idx_base + index in the document)
+  uint32_t d;     // its document
+  uint32_t rel;   // its index in the document
+};
 __global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
+  __shared__ NumEntry q[kNumThreads / 32][64];
   const int lane = threadIdx.x & 31;
   uint8_t *my = win[threadIdx.x];
-  const uint32_t n_tiles = J.counters[2];
-  const uint32_t warps = gridDim.x * (kNumThreads / 32);
-  for (uint32_t t = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
-    const uint32_t d = doc_of_tile(J, t);
-    const uint32_t nidx = J.doc_nidx[d];
-    if ((J.doc_flags[d] & kDocBad) || nidx == 0) continue;
-    const uint32_t m = J.tile_nnum[t];
-    if (m == 0) continue;
-    const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
-    const uint8_t *doc = J.base + J.doc_off[d];
-    const uint64_t ib = idx_base(J, d);
-    const uint32_t off = J.tile_off[t];
-    for (uint32_t k = lane; k < m; k += 32) {
-      const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
-      const uint64_t pos = J.idx[ib + rel];
-      const uint64_t nxt = rel + 1 < nidx ? J.idx[ib + rel + 1] : len;
+  NumEntry *wq = q[threadIdx.x >> 5];
+  uint32_t head = 0, tail = 0;
+  auto flush = [&]() {
+    const uint32_t m = min(32u, tail - head);
+    if ((uint32_t)lane < m) {
+      const NumEntry e = wq[(head + lane) & 63u];
+      const uint64_t len = J.doc_off[e.d + 1] - J.doc_off[e.d];
+      const uint8_t *doc = J.base + J.doc_off[e.d];
+      const uint32_t nidx = J.doc_nidx[e.d];
+      const uint64_t pos = J.idx[e.slot];
+      const uint64_t nxt = e.rel + 1 < nidx ? J.idx[e.slot + 1] : len;
       const uint64_t wend = min(len, pos + kNumWindow);
       uint8_t tag = 0;
       uint64_t v = 0;
@@ -456,13 +459,37 @@ __global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restr
         nc = parse_number(doc + pos, doc + len, tag, v);
       }
       if (nc) {
-        J.slen[ib + rel] = kSlenErr | (uint32_t)nc;
+        J.slen[e.slot] = kSlenErr | (uint32_t)nc;
       } else {
-        J.slen[ib + rel] = tag;
-        J.numv[ib + rel] = v;
+        J.slen[e.slot] = tag;
+        J.numv[e.slot] = v;
       }
     }
+    head += m;
+    __syncwarp();
+  };
+  const uint32_t n_tiles = J.counters[2];
+  const uint32_t warps = gridDim.x * (kNumThreads / 32);
+  for (uint32_t t = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+    const uint32_t d = doc_of_tile(J, t);
+    if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
+    const uint32_t m = J.tile_nnum[t];
+    if (m == 0) continue;
+    const uint64_t ib = idx_base(J, d);
+    const uint32_t off = J.tile_off[t];
+    for (uint32_t k0 = 0; k0 < m; k0 += 32) {
+      const uint32_t k = k0 + lane;
+      const uint32_t c = min(32u, m - k0);
+      if ((uint32_t)lane < c) {
+        const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
+        wq[(tail + lane) & 63u] = NumEntry{ib + rel, d, rel};
+      }
+      tail += c;
+      __syncwarp();
+      if (tail - head >= 32) flush();
+    }
   }
+  while (head != tail) flush();
 }
 
 // ---------------------------------------------------------------------------
