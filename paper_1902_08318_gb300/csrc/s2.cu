@@ -774,13 +774,27 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
             tape[tp + 1] = nv;
           }
         } else if (is_atom(k)) {
-          const char *word = k == K_TRUE ? "true" : (k == K_FALSE ? "false" : "null");
+          // the literal and the byte after it: one 8-byte window of the staged
+          // tile (two aligned words and a funnel shift), else byte by byte
           const uint32_t nw = k == K_FALSE ? 5 : 4;
+          const uint64_t lit = k == K_TRUE ? 0x65757274ull : (k == K_FALSE ? 0x65736C6166ull : 0x6C6C756Eull);
           bool ok = pos + nw <= len;
-          for (uint32_t i = 0; ok && i < nw; i++) ok = sv.at(pos + i) == (uint8_t)word[i];
-          if (ok && pos + nw < len) ok = is_terminator(sv.at(pos + nw));
+          if (ok) {
+            if (pos + 8 <= sv.slimit) {
+              const uintptr_t ua = (uintptr_t)(sv.smem + (pos - sv.sbase));
+              const uint32_t *wp = reinterpret_cast<const uint32_t *>(ua & ~(uintptr_t)3);
+              const uint32_t sh = (uint32_t)(ua & 3u) * 8;
+              const uint64_t x = ((uint64_t)__funnelshift_r(wp[1], wp[2], sh) << 32) |
+                                 __funnelshift_r(wp[0], wp[1], sh);
+              ok = (x & ((1ull << (8 * nw)) - 1)) == lit &&
+                   (pos + nw >= len || is_terminator((uint8_t)(x >> (8 * nw))));
+            } else {
+              for (uint32_t i = 0; ok && i < nw; i++) ok = sv.at(pos + i) == (uint8_t)(lit >> (8 * i));
+              if (ok && pos + nw < len) ok = is_terminator(sv.at(pos + nw));
+            }
+          }
           if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
-          else if (tp < tape_cap) tape[tp] = (uint64_t)word[0] << 56;
+          else if (tp < tape_cap) tape[tp] = (uint64_t)(uint8_t)lit << 56;
         }
         if (code) report(J, d, g, code);
       }
