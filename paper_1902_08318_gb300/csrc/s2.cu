@@ -41,6 +41,7 @@ constexpr int kStrStage = 2048;                // string output of 32 strings, s
                                                // of strings are written directly)
 constexpr uint32_t kQueue = 64;                // per-warp work queues (ring buffers)
 constexpr uint32_t kFrontSmem = 64;            // frontier slots of a tile kept in shared memory
+constexpr uint32_t kTileHasEscapes = 0x80000000u;  // flag in tile_nnum
 
 // A string's entry in `slen`: an error code, or its normalised length and
 // whether it holds escapes (then the reduce pass has left its normalised bytes
@@ -110,6 +111,34 @@ __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc,
   v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
   v.smem = bytes;
   return v;
+}
+
+// stage_tile's copy without waiting: each lane starts asynchronous 16-byte
+// copies (cp.async) into shared memory; wait_staged() completes them.
+template <int STAGE = kStageBytes>
+__device__ __forceinline__ Staged stage_tile_async(uint8_t *bytes, const uint8_t *doc,
+                                                   uint64_t len, uint64_t t0, int lane) {
+  const uintptr_t g0 = (uintptr_t)(doc + t0);
+  const uintptr_t a0 = g0 & ~(uintptr_t)15;
+  const uintptr_t dend = (uintptr_t)doc + len;
+  const uintptr_t send = min((uintptr_t)(a0 + STAGE), dend);
+  const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
+  for (uint32_t c = lane; c < nch; c += 32) {
+    const uint32_t sa = (uint32_t)__cvta_generic_to_shared(bytes + 16 * c);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(sa), "l"(a0 + 16 * c) : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+  Staged v;
+  v.doc = doc;
+  v.len = len;
+  v.sbase = (int64_t)t0 - (int64_t)(g0 - a0);
+  v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
+  v.smem = bytes;
+  return v;
+}
+__device__ __forceinline__ void wait_staged() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncwarp();
 }
 
 // Position of the token after each token of a chunk (the next index, or the
@@ -296,6 +325,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     uint64_t sb = 0;  // string-buffer bytes of this lane's strings without escapes
     uint32_t shead = 0, stail = 0;
     uint32_t nnum = 0;  // number tokens of the tile so far (listed for numbers_kernel)
+    const uint32_t wtail0 = wtail;  // escaped strings queued before this tile
     // strings: the next 32 queued get their length from the masks; those the
     // masks cannot decide go to the walk queue
     auto flush_strings = [&]() {
@@ -400,7 +430,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     for (int32_t v = max(mn, -kLevelOff) + lane; v <= min(mx, kLevelOff); v += 32) ot.at(v) = 0;
     __syncwarp();
     if (lane == 0) {
-      J.tile_nnum[t] = nnum;
+      // bit 31: the tile has strings with escapes (the build pass stages its
+      // scratch window ahead)
+      J.tile_nnum[t] = nnum | (wtail != wtail0 ? kTileHasEscapes : 0u);
       S2Agg &a = J.s2_rec[t];
       a.dd = depth;
       a.mn = mn;
@@ -473,7 +505,7 @@ __global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restr
   for (uint32_t t = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
-    const uint32_t m = J.tile_nnum[t];
+    const uint32_t m = J.tile_nnum[t] & ~kTileHasEscapes;
     if (m == 0) continue;
     const uint64_t ib = idx_base(J, d);
     const uint32_t off = J.tile_off[t];
@@ -617,8 +649,11 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
     const Staged sv = stage_tile<kStageBytesB>(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
     uint32_t shead = 0, stail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
-    Staged us{};  // the scratch window, staged at the first string with escapes
-    bool us_staged = false;
+    // the scratch window, copied ahead when the tile has strings with escapes
+    const bool has_esc = (J.tile_nnum[t] & kTileHasEscapes) != 0;
+    Staged us{};
+    if (has_esc) us = stage_tile_async<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
+    bool us_ready = !has_esc;
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
     // numbers (Sec. 3.2.1), 32 at a time
@@ -648,9 +683,9 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
       if (is_str && tp < tape_cap) tape[tp] = ((uint64_t)'"' << 56) | so;
       // Strings with escapes take their normalised bytes from the scratch
       // buffer of the reduce pass (same positions), staged once per tile.
-      if (!us_staged && __any_sync(0xFFFFFFFFu, is_str && walk)) {
-        us = stage_tile<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
-        us_staged = true;
+      if (!us_ready && __any_sync(0xFFFFFFFFu, is_str && walk)) {
+        wait_staged();
+        us_ready = true;
       }
       const Staged &src = walk ? us : sv;
       const bool fits = !is_str || (n < kSlenLen && p0 + n <= src.slimit);
@@ -804,6 +839,7 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
       if (stail - shead >= 32) flush_strings();
     }
     while (shead != stail) flush_strings();
+    if (!us_ready) wait_staged();  // no copy may still be in flight into ubytes
     __syncwarp();  // every lane is done with this tile's staged bytes
   }
 }
