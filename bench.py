@@ -12,7 +12,9 @@ nested to depth 1024): larger than L2, so no flush is needed between steps.
 `value` is whole-job input GB/s over K steps timed with CUDA events on the
 launching stream (max over ranks).  `e2e` is the same metric through sj_parse
 with a pinned host buffer (host-to-device copy inside every step, result
-header read back).  `roofline` reports the dominant kernel against the
+header read back); a document larger than the parser's largest chunk is
+copied in chunks on a second stream while the kernels parse the chunks that
+have landed.  `roofline` reports the dominant kernel against the
 measured HBM copy bandwidth; `cpu_baseline` times the CPU oracle on a bounded
 sample of the same workload on this host's cores.
 
@@ -313,7 +315,11 @@ def report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_s
                           "input_frac": round(B / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "e2e": {"value": round(e2e, 3) if e2e == e2e else None, "unit": "GB/s",
-                "h2d_bytes_per_step": B, "d2h_bytes_per_step": 56},
+                "h2d_bytes_per_step": B, "d2h_bytes_per_step": 56,
+                "path": ("pinned host document copied in chunks (first 32 MiB, doubling up to "
+                         "512 MiB) on a second stream, parsed as the chunks land"
+                         if B > (512 << 20) else
+                         "pinned host document read by stage 1 over the host link")},
         "gpu_launches": kernels_per_run * args.steps,
         "clocks": clk,
     }

@@ -223,8 +223,24 @@ sj_status sj_server_replay(sj_server *s, const uint8_t *bytes, const uint64_t *o
 sj_status sj_parser_set_profiling(sj_parser *p, int enable);
 sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
 
-/* Number of kernel launches in one run of this parser. */
+/* Number of kernel launches in one run of this parser (over resident input,
+ * or host input that is not chunked). */
 int sj_parser_kernels_per_run(const sj_parser *p);
+
+/* Host documents that arrive in chunks.  A single document in pinned host
+ * memory (cudaMallocHost / cudaHostRegister) longer than chunk_bytes is
+ * parsed while it is copied: a second stream copies it chunk by chunk, and
+ * the run's stream runs stage 1 on each chunk once it has landed and stage 2
+ * on every tile whose tokens end in bytes that have landed (Sec. 3 notes that
+ * the two stages can be interleaved over a stream of chunks).  Results are
+ * identical to a parse of the same bytes in device memory.  chunk_bytes is
+ * the largest chunk, rounded up to a multiple of 2048: the first chunk is
+ * 1/16 of it and each next one doubles up to it; at most 64 chunks, the last
+ * taking what remains.  0 turns chunking off (stage 1 then reads the pinned
+ * document over the host link itself); the default is 512 MiB.  Such runs
+ * launch their kernels directly (no graph; about 20 launches per chunk) and
+ * are not profiled: with profiling on, the document is not chunked. */
+sj_status sj_parser_set_host_chunk(sj_parser *p, uint64_t chunk_bytes);
 
 /* Launch shapes.  The four main kernels (stage-1 blocks, stage-1 flatten,
  * stage-2 reduce, stage-2 build) loop over tiles, so any grid covers any

@@ -136,6 +136,8 @@ def load(path: str | None = None):
     lib.sj_parser_stage_times.restype = ctypes.c_int
     lib.sj_parser_kernels_per_run.argtypes = [vp]
     lib.sj_parser_kernels_per_run.restype = ctypes.c_int
+    lib.sj_parser_set_host_chunk.argtypes = [vp, u64]
+    lib.sj_parser_set_host_chunk.restype = ctypes.c_int
     lib.sj_stage1_indices_noalloc.argtypes = [vp, u64, vp, vp, vp]
     lib.sj_stage1_indices_noalloc.restype = ctypes.c_int
     lib.sj_error_name.argtypes = [ctypes.c_int]
@@ -196,7 +198,8 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_server_destroy", "sj_server_slots", "sj_server_device_bytes", "sj_server_batches",
             "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay",
             "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune",
-            "sj_query_create", "sj_query_destroy", "sj_query_distinct"]
+            "sj_query_create", "sj_query_destroy", "sj_query_distinct",
+            "sj_parser_set_host_chunk"]
 TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
           "s2_numbers", "s2_build", "finalize")
@@ -344,6 +347,11 @@ class Parser:
 
     def kernels_per_run(self) -> int:
         return int(self._lib.sj_parser_kernels_per_run(self._h))
+
+    def set_host_chunk(self, chunk_bytes: int):
+        """Chunk size for single documents in pinned host memory, parsed while
+        they are copied (0: never chunk)."""
+        _check(self._lib.sj_parser_set_host_chunk(self._h, int(chunk_bytes)))
 
     @staticmethod
     def view(ptr: int, n: int, typestr: str):

@@ -6,6 +6,11 @@
 // bracketed by a host-to-device copy of the run descriptor and the document
 // offsets and a device-to-host copy of the results.  The sequence is captured
 // once per (parser, bucket of document counts) as a CUDA graph and replayed.
+//
+// One large document in pinned host memory is parsed as it arrives
+// (enqueue_chunked): a second stream copies it chunk by chunk while the
+// kernels run stage 1 on each chunk that has landed and stage 2 on every tile
+// whose tokens are known to end in landed bytes.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -25,6 +30,8 @@ __global__ void finalize_kernel(const Job *job);
 __global__ void spt_build_kernel(const Job *job, uint32_t src);
 __global__ void jump_kernel(const Job *job);
 __global__ void frontier_kernel(const Job *job);
+__global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, int stage2,
+                                   int last);
 void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
 void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
 }  // namespace sj
@@ -83,7 +90,7 @@ struct sj_parser {
   int num_grid = 0;
   int sms = 0;
   int occ[4] = {1, 1, 1, 1};  // most resident blocks per SM: s1 blocks, flatten, reduce, build
-  uint32_t scan_blocks = 0, spt_levels = 0;
+  uint32_t scan_blocks = 0, scan_grid = 0, spt_levels = 0;
   uint64_t device_bytes = 0;  // cudaMalloc'ed by this parser
   // graph cache: one captured run per document-count bucket (powers of two)
   static constexpr int kBuckets = 33;
@@ -92,6 +99,13 @@ struct sj_parser {
   cudaEvent_t done = nullptr;
   static constexpr int kStages = 9;
   cudaEvent_t prof[kStages + 1] = {};
+  // chunked runs over a host document
+  static constexpr uint32_t kMaxChunks = 64;
+  uint64_t host_chunk = 512ull << 20;  // largest chunk; 0 = never chunk
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_chunk[kMaxChunks] = {};
+  bool chunked_run = false;
   bool profiling = false;
   bool profiled_run = false;
   bool pending = false;  // an async parse is in flight
@@ -123,6 +137,10 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
   for (cudaGraphExec_t g : p->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  for (cudaEvent_t e : p->ev_chunk)
+    if (e) cudaEventDestroy(e);
   if (p->done) cudaEventDestroy(p->done);
   for (cudaEvent_t e : p->prof)
     if (e) cudaEventDestroy(e);
@@ -151,8 +169,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_input, max_bytes + 64))) return r;
   if ((r = dalloc(p, &p->d_doc_off, (uint64_t)max_docs + 1))) return r;
   if ((r = dalloc(p, &p->d_tile_first, (uint64_t)max_docs + 1))) return r;
-  if ((r = dalloc(p, &p->d_counters, 4))) return r;
+  if ((r = dalloc(p, &p->d_counters, sj::kCounters))) return r;
   p->scan_blocks = (uint32_t)((tiles + sj::kScanBlock - 1) / sj::kScanBlock);
+  p->scan_grid = 0;  // set with the SM count below
   p->spt_levels = 2;
   while ((1ull << (p->spt_levels - 1)) <= tiles) p->spt_levels++;
   if ((r = dalloc(p, &p->d_tile_cnt, tiles))) return r;
@@ -184,13 +203,16 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_doc_str, max_docs))) return r;
   if ((r = dalloc(p, &p->d_results, max_docs))) return r;
   if ((r = dalloc(p, &p->d_job, 1))) return r;
-  CK(cudaMemset(p->d_counters, 0, 4 * sizeof(uint32_t)));
+  CK(cudaMemset(p->d_counters, 0, sj::kCounters * sizeof(uint32_t)));
   CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
   CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
   CK(cudaMallocHost((void **)&p->h_results, (size_t)max_docs * sizeof(sj_doc_result)));
   CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
+  CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+  for (cudaEvent_t &e : p->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   int sms = 0, occ1 = 0, occf = 0, occ2r = 0, occ2b = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -203,6 +225,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2b, sj::stage2_build_kernel,
                                                    sj::kS2Threads, 0));
   p->sms = sms;
+  p->scan_grid = p->scan_blocks < (uint32_t)(2 * sms) ? p->scan_blocks : (uint32_t)(2 * sms);
   p->occ[0] = occ1 > 0 ? occ1 : 1;
   p->occ[1] = occf > 0 ? occf : 1;
   p->occ[2] = occ2r > 0 ? occ2r : 1;
@@ -283,19 +306,19 @@ extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint3
 
 // The kernels of one run, in order.  With `ev`, an event is recorded before
 // the first kernel and after each of the stages named in STAGE_NAMES.
-static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
-  if (ev) cudaEventRecord(ev[0], s);
-  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
-  if (ev) cudaEventRecord(ev[1], s);
+static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::stage1_blocks_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[2], s);
-  sj::launch_scan1(p->d_job, p->scan_blocks, s);
+  sj::launch_scan1(p->d_job, p->scan_grid, s);
   if (ev) cudaEventRecord(ev[3], s);
   sj::stage1_flatten_kernel<<<p->fl_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
+}
+
+static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
-  sj::launch_scan2(p->d_job, p->scan_blocks, s);
+  sj::launch_scan2(p->d_job, p->scan_grid, s);
   for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
     sj::spt_build_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job, src);
   sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
@@ -305,6 +328,14 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[7], s);
   sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);
+}
+
+static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+  if (ev) cudaEventRecord(ev[0], s);
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[1], s);
+  enqueue_stage1(p, s, ev);
+  enqueue_stage2(p, s, ev);
   sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[9], s);
 }
@@ -380,23 +411,79 @@ static int wait_pending(sj_parser *p) {
   return SJ_SUCCESS;
 }
 
+// One document of `len` bytes in pinned host memory, parsed while it is copied
+// (Sec. 3: stage 1 and stage 2 may run over a stream of chunks).  The copy
+// stream moves the chunks in order, each followed by an event; the run's
+// stream waits for chunk c, runs stage 1 on its tiles (the tile scans carry
+// the state of the tiles before), then stage 2 on the tiles the device found
+// ready (chunk_range_kernel), and after the last chunk on all that remain.
+static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cudaStream_t s) {
+  // Chunk sizes: a small first chunk (nothing overlaps its copy), then
+  // doubling up to host_chunk; the copies run about twice as fast as the
+  // parse, so each chunk lands before the kernels reach it.  The last of
+  // kMaxChunks chunks takes whatever remains.
+  const uint64_t tile = sj::kTileBytes;
+  const uint64_t cmax = p->host_chunk;
+  uint64_t sz = (cmax / 16 + tile - 1) / tile * tile;
+  uint64_t at[sj_parser::kMaxChunks + 1];
+  uint32_t nc = 0;
+  at[0] = 0;
+  while (at[nc] < len) {
+    const uint64_t o = at[nc];
+    const uint64_t n = nc + 1 == sj_parser::kMaxChunks || len - o < sz ? len - o : sz;
+    at[++nc] = o + n;
+    sz = sz * 2 < cmax ? sz * 2 : cmax;
+  }
+  CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  // the input buffer is free once the work queued before this run is done
+  CK(cudaEventRecord(p->ev_start, s));
+  CK(cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0));
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaMemcpyAsync(p->d_input + at[c], host + at[c], at[c + 1] - at[c], cudaMemcpyHostToDevice,
+                       p->copy_stream));
+    CK(cudaEventRecord(p->ev_chunk[c], p->copy_stream));
+  }
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaStreamWaitEvent(s, p->ev_chunk[c], 0));
+    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, (uint32_t)(at[c] / tile),
+                                            (uint32_t)((at[c + 1] + tile - 1) / tile), 0, 0);
+    enqueue_stage1(p, s, nullptr);
+    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 1, c + 1 == nc);
+    enqueue_stage2(p, s, nullptr);
+  }
+  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
+  return SJ_SUCCESS;
+}
+
 // Queue one run over n_docs documents whose offsets are in h_doc_off.
 static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n_docs,
                   cudaStream_t stream) {
   int r;
   if ((r = wait_pending(p))) return r;
   const uint8_t *base = bytes, *src = nullptr;
+  bool chunked = false;
   if (!is_device_ptr(bytes)) {
-    // one document in pinned host memory: stage 1 reads it over the host link
-    // and writes the device copy; otherwise copy it first
+    // one document in pinned host memory: parsed while it is copied when it
+    // spans several chunks, else stage 1 reads it over the host link and
+    // writes the device copy; any other host input is copied first
     src = n_docs == 1 && total ? pinned_device_ptr(bytes) : nullptr;
-    if (!src) CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
+    chunked = src && p->host_chunk && total > p->host_chunk && !p->profiling;
+    if (chunked) src = nullptr;
+    else if (!src) CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
     base = p->d_input;
   }
   p->h_job->base = base;
   p->h_job->src = src;
   p->h_job->n_docs = n_docs;
-  if (p->profiling) {
+  p->chunked_run = chunked;
+  if (chunked) {
+    if ((r = enqueue_chunked(p, bytes, total, stream))) return r;
+    p->profiled_run = false;
+  } else if (p->profiling) {
     // the same sequence as the graph, with events between the kernels
     CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
@@ -530,6 +617,14 @@ extern "C" sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n) {
   CK(cudaEventSynchronize(p->prof[sj_parser::kStages]));
   for (int i = 0; i < sj_parser::kStages; i++)
     CK(cudaEventElapsedTime(&ms[i], p->prof[i], p->prof[i + 1]));
+  return SJ_SUCCESS;
+}
+
+extern "C" sj_status sj_parser_set_host_chunk(sj_parser *p, uint64_t chunk_bytes) {
+  if (!p) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  p->host_chunk = (chunk_bytes + sj::kTileBytes - 1) / sj::kTileBytes * sj::kTileBytes;
   return SJ_SUCCESS;
 }
 

@@ -97,9 +97,10 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
   __shared__ uint32_t s_words[kS1Warps * 32][16];  // one block per thread (byte reads)
   const int lane = threadIdx.x & 31;
   uint32_t *my_words = s_words[threadIdx.x];
-  const uint32_t n_tiles = J.counters[2];
+  uint32_t t_lo, t_hi;
+  s1_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * kS1Warps;
-  for (uint32_t t = blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  for (uint32_t t = t_lo + blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
@@ -213,9 +214,10 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job
   __shared__ uint32_t stage[kS1Warps][kTileBytes];
   const int lane = threadIdx.x & 31;
   uint32_t *out_stage = stage[threadIdx.x >> 5];
-  const uint32_t n_tiles = J.counters[2];
+  uint32_t t_lo, t_hi;
+  s1_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * kS1Warps;
-  for (uint32_t t = blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  for (uint32_t t = t_lo + blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint32_t ntiles_d = J.tile_first[d + 1] - J.tile_first[d];
@@ -247,6 +249,8 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job
       if (tt == ntiles_d - 1) {
         J.doc_nidx[d] = pre.base + n;
         if (pre.q_in ^ J.s1_rec[t].qpar) atomicOr(&J.doc_flags[d], kFlagUnclosed);
+      } else if (t + 1 == t_hi) {
+        J.doc_nidx[d] = pre.base + n;  // the indices so far (a document arriving in chunks)
       }
     }
   }

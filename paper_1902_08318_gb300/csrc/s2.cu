@@ -257,7 +257,8 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
   for (uint32_t i = lane; i < kOpenSmem; i += 32) W.open[i] = 0;
   __syncthreads();
   uint16_t *const open_g = J.open_g + (uint64_t)(blockIdx.x * kS2Warps + wid) * kOpenGlobal;
-  const uint32_t n_tiles = J.counters[2];
+  uint32_t t_lo, t_hi;
+  s2_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * kS2Warps;
   // Strings with escapes are walked (Sec. 3.2.2) 32 at a time, across tiles:
   // a tile holds too few of them to fill a warp.  The walk reads the staged
@@ -289,7 +290,7 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     whead += m;
     __syncwarp();
   };
-  for (uint32_t t = blockIdx.x * kS2Warps + wid; t < n_tiles; t += warps) {
+  for (uint32_t t = t_lo + blockIdx.x * kS2Warps + wid; t < t_hi; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -500,9 +501,10 @@ __global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restr
     head += m;
     __syncwarp();
   };
-  const uint32_t n_tiles = J.counters[2];
+  uint32_t t_lo, t_hi;
+  s2_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * (kNumThreads / 32);
-  for (uint32_t t = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  for (uint32_t t = t_lo + blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < t_hi; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
     const uint32_t m = J.tile_nnum[t] & ~kTileHasEscapes;
@@ -607,10 +609,11 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
   __syncthreads();
   const int lane = threadIdx.x & 31;
   BuildSmem &W = WS[threadIdx.x >> 5];
-  const uint32_t n_tiles = J.counters[2];
+  uint32_t t_lo, t_hi;
+  s2_range(J, t_lo, t_hi);
   const uint32_t max_depth = J.max_depth;
   const uint32_t warps = gridDim.x * kS2Warps;
-  for (uint32_t t = blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < n_tiles; t += warps) {
+  for (uint32_t t = t_lo + blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -895,7 +898,43 @@ __global__ void __launch_bounds__(1024) setup_kernel(const Job *__restrict__ job
   if (tid == 0) {
     J.tile_first[J.n_docs] = s_carry;
     J.counters[2] = s_carry;
+    J.counters[4] = 0;  // both stages: all tiles
+    J.counters[5] = s_carry;
+    J.counters[6] = 0;
+    J.counters[7] = s_carry;
   }
+}
+
+// A document that arrives in chunks (one document; host input): the tiles of
+// the next stage-1 launches are [lo1, hi1).  With `stage2`, the tiles of the
+// next stage-2 launches start where the previous ones stopped and end before
+// the tile holding the last index found so far: each token of those tiles is
+// followed by a known index, so its bytes, and the staged bytes and masks
+// after its tile, lie in chunks that have arrived and passed stage 1.  With
+// `last` they run to the end of the document.
+__global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, uint32_t hi1,
+                                   int stage2, int last) {
+  const Job &J = *job;
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  if (!stage2) {
+    J.counters[4] = min(lo1, J.counters[2]);
+    J.counters[5] = min(hi1, J.counters[2]);
+    if (lo1 == 0) {  // the first chunk: no stage-2 tile is done yet
+      J.counters[6] = 0;
+      J.counters[7] = 0;
+    }
+    return;
+  }
+  const uint32_t lo = J.counters[7];
+  uint32_t hi = lo;
+  if (last) {
+    hi = J.counters[2];
+  } else if (J.n_docs == 1 && !(J.doc_flags[0] & kDocBad)) {
+    const uint32_t n = J.doc_nidx[0];
+    if (n) hi = J.tile_first[0] + J.idx[idx_base(J, 0) + n - 1] / (uint32_t)kTileBytes;
+  }
+  J.counters[6] = lo;
+  J.counters[7] = max(hi, lo);
 }
 
 // Per-document results (error precedence: capacity, empty, UTF-8, unclosed

@@ -32,6 +32,12 @@ struct M1 {
     return r;
   }
   __device__ static T load(const Job &J, uint32_t t) { return J.s1_rec[t]; }
+  __device__ static void range(const Job &J, uint32_t &lo, uint32_t &hi) { s1_range(J, lo, hi); }
+  // the exclusive prefix of tile t as stored (c1 is never read back)
+  __device__ static T stored(const Job &J, uint32_t t) {
+    const S1Pre p = J.s1_pre[t];
+    return T{p.q_in, p.base, 0, 0};
+  }
   __device__ static void store(const Job &J, uint32_t t, const T &excl, const T &) {
     J.s1_pre[t] = S1Pre{excl.c0, excl.qpar};  // documents start outside strings
   }
@@ -60,6 +66,12 @@ struct M2 {
     return r;
   }
   __device__ static T load(const Job &J, uint32_t t) { return J.s2_rec[t]; }
+  __device__ static void range(const Job &J, uint32_t &lo, uint32_t &hi) { s2_range(J, lo, hi); }
+  // the exclusive prefix of tile t as stored (mn is never read back)
+  __device__ static T stored(const Job &J, uint32_t t) {
+    const S2Pre p = J.s2_pre[t];
+    return T{p.d_start, 0, p.tape_start - 1u, 0, p.str_start};
+  }
   __device__ static void store(const Job &J, uint32_t t, const T &excl, const T &self) {
     S2Pre p;
     p.d_start = excl.dd;
@@ -100,18 +112,23 @@ __device__ typename M::T block_inclusive(typename M::T v, typename M::T *s_warp,
   return v;
 }
 
+// Scan block b covers tiles [lo + b * kScanBlock, lo + (b + 1) * kScanBlock)
+// of the launch's range; thread blocks loop over scan blocks, so a grid of a
+// few blocks per SM serves a whole document or one chunk of it alike.
 template <class M>
 __global__ void __launch_bounds__(kScanBlock) scan_up_kernel(const Job *__restrict__ job) {
   using T = typename M::T;
   const Job &J = *job;
   __shared__ T s_warp[32];
-  const uint32_t n = J.counters[2];
-  const uint32_t t = blockIdx.x * kScanBlock + threadIdx.x;
-  if (blockIdx.x * kScanBlock >= n) return;
-  T v = t < n ? M::load(J, t) : M::identity();
-  T total;
-  block_inclusive<M>(v, s_warp, total);
-  if (threadIdx.x == 0) reinterpret_cast<T *>(J.scan_agg)[blockIdx.x] = total;
+  uint32_t lo, n;
+  M::range(J, lo, n);
+  for (uint32_t b = blockIdx.x; lo + b * kScanBlock < n; b += gridDim.x) {
+    const uint32_t t = lo + b * kScanBlock + threadIdx.x;
+    T v = t < n ? M::load(J, t) : M::identity();
+    T total;
+    block_inclusive<M>(v, s_warp, total);
+    if (threadIdx.x == 0) reinterpret_cast<T *>(J.scan_agg)[b] = total;
+  }
 }
 
 template <class M>
@@ -121,8 +138,13 @@ __global__ void __launch_bounds__(kScanBlock) scan_top_kernel(const Job *__restr
   __shared__ T s_warp[32];
   __shared__ T s_incl[kScanBlock];
   __shared__ T s_carry;
-  const uint32_t nb = (J.counters[2] + kScanBlock - 1) / kScanBlock;
-  if (threadIdx.x == 0) s_carry = M::identity();
+  uint32_t lo, hi;
+  M::range(J, lo, hi);
+  const uint32_t nb = (hi - lo + kScanBlock - 1) / kScanBlock;
+  // tiles before the range (earlier chunks of the document) are done: their
+  // inclusive prefix is the carry into the range
+  if (threadIdx.x == 0)
+    s_carry = lo == 0 ? M::identity() : M::combine(M::stored(J, lo - 1), M::load(J, lo - 1));
   __syncthreads();
   for (uint32_t base = 0; base < nb; base += kScanBlock) {
     const uint32_t b = base + threadIdx.x;
@@ -147,23 +169,27 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
   const Job &J = *job;
   __shared__ T s_warp[32];
   __shared__ T s_incl[kScanBlock];
-  const uint32_t n = J.counters[2];
-  const uint32_t t = blockIdx.x * kScanBlock + threadIdx.x;
-  if (blockIdx.x * kScanBlock >= n) return;
-  const T self = t < n ? M::load(J, t) : M::identity();
-  T total;
-  const T incl = block_inclusive<M>(self, s_warp, total);
-  s_incl[threadIdx.x] = incl;
-  __syncthreads();
-  if (t >= n) return;
-  T excl;
-  if (self.head) {
-    excl = M::identity();
-  } else {
-    const T pre = reinterpret_cast<const T *>(J.scan_pre)[blockIdx.x];
-    excl = threadIdx.x ? M::combine(pre, s_incl[threadIdx.x - 1]) : pre;
+  uint32_t lo, n;
+  M::range(J, lo, n);
+  for (uint32_t b = blockIdx.x; lo + b * kScanBlock < n; b += gridDim.x) {
+    const uint32_t t = lo + b * kScanBlock + threadIdx.x;
+    const T self = t < n ? M::load(J, t) : M::identity();
+    T total;
+    const T incl = block_inclusive<M>(self, s_warp, total);
+    s_incl[threadIdx.x] = incl;
+    __syncthreads();
+    if (t < n) {
+      T excl;
+      if (self.head) {
+        excl = M::identity();
+      } else {
+        const T pre = reinterpret_cast<const T *>(J.scan_pre)[b];
+        excl = threadIdx.x ? M::combine(pre, s_incl[threadIdx.x - 1]) : pre;
+      }
+      M::store(J, t, excl, self);
+    }
+    __syncthreads();  // s_incl is reused by the next scan block
   }
-  M::store(J, t, excl, self);
 }
 
 template __global__ void scan_up_kernel<M1>(const Job *);
@@ -189,9 +215,10 @@ void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s) {
 // launch derives four levels from level `src` (sixteen reads per tile).
 __global__ void spt_build_kernel(const Job *__restrict__ job, uint32_t src) {
   const Job &J = *job;
-  const uint32_t n = J.counters[2];
+  uint32_t lo, n;
+  s2_range(J, lo, n);
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+  for (uint32_t t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
     if (src == 0) J.spt[t] = J.s2_pre[t].low;
     if (src + 1 >= J.spt_levels) continue;
     const int32_t *in = J.spt + (uint64_t)src * J.spt_stride;
@@ -221,9 +248,10 @@ __device__ __forceinline__ int64_t last_lower(const Job &J, int64_t from, int64_
 
 __global__ void jump_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  const uint32_t n = J.counters[2];
+  uint32_t lo, n;
+  s2_range(J, lo, n);
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t t = blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
+  for (uint32_t t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
     const uint32_t d = doc_of_tile(J, t);
     const int64_t c = last_lower(J, (int64_t)t - 1, J.tile_first[d], J.s2_pre[t].low);
     J.s2_pre[t].jump = c < 0 ? kNoTile : (uint32_t)c;
@@ -242,10 +270,11 @@ __global__ void jump_kernel(const Job *__restrict__ job) {
 // each range with all lanes.
 __global__ void frontier_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  const uint32_t n = J.counters[2];
+  uint32_t lo, n;
+  s2_range(J, lo, n);
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t t = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n; t += nw) {
+  for (uint32_t t = lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < n; t += nw) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     if (J.doc_flags[d] & (kFlagUtf8 | kFlagUnclosed | kFlagCapacity)) continue;

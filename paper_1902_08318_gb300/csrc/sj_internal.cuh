@@ -66,7 +66,7 @@ struct Job {
   uint64_t max_doc_len;
   // scratch
   uint32_t *tile_first;     // n_docs + 1: first stage-1 tile of each document
-  uint32_t *counters;       // [0] look-back ticket, [2] number of tiles
+  uint32_t *counters;       // [0] look-back ticket, [2] number of tiles, [4..7] tile ranges
   uint32_t *s1_state;       // per tile: escape/quote/separator look-back word
   uint64_t *s1_count;       // per tile: index-count look-back word
   uint32_t *tile_cnt;       // per tile: indices produced
@@ -102,6 +102,20 @@ struct Job {
   uint64_t *doc_str;
   sj_doc_result *results;
 };
+
+// Tile ranges of the launches: stage-1 kernels work on tiles [counters[4],
+// counters[5]), stage-2 kernels on [counters[6], counters[7]).  A run over
+// resident input sets both to all tiles; a run over a host document that
+// arrives in chunks moves them forward chunk by chunk (chunk_range_kernel).
+constexpr int kCounters = 8;
+__device__ __forceinline__ void s1_range(const Job &J, uint32_t &lo, uint32_t &hi) {
+  lo = J.counters[4];
+  hi = J.counters[5];
+}
+__device__ __forceinline__ void s2_range(const Job &J, uint32_t &lo, uint32_t &hi) {
+  lo = J.counters[6];
+  hi = J.counters[7];
+}
 
 // Output placement: each document gets capacity proportional to its length.
 __device__ __forceinline__ uint64_t rel_off(const Job &J, uint32_t d) {
