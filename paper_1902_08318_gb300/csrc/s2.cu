@@ -246,7 +246,7 @@ __device__ __forceinline__ bool plain_string_len(const ReduceSmem &W, uint64_t t
   return false;
 }
 
-__global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__restrict__ job) {
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ ReduceSmem WS[kS2Warps];
   __shared__ uint8_t s_kind[256];
@@ -259,7 +259,6 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
   uint16_t *const open_g = J.open_g + (uint64_t)(blockIdx.x * kS2Warps + wid) * kOpenGlobal;
   uint32_t t_lo, t_hi;
   s2_range(J, t_lo, t_hi);
-  const uint32_t warps = gridDim.x * kS2Warps;
   // Strings with escapes are walked (Sec. 3.2.2) 32 at a time, across tiles:
   // a tile holds too few of them to fill a warp.  The walk reads the staged
   // bytes while its string is in the current tile, else global memory, and
@@ -290,7 +289,9 @@ __global__ void __launch_bounds__(kS2Threads) stage2_reduce_kernel(const Job *__
     whead += m;
     __syncwarp();
   };
-  for (uint32_t t = t_lo + blockIdx.x * kS2Warps + wid; t < t_hi; t += warps) {
+  uint32_t tk = __shfl_sync(0xFFFFFFFFu, draw_ticket(J, kTicketReduce, lane), 0);
+  for (uint32_t t = t_lo + tk; t < t_hi; t = t_lo + __shfl_sync(0xFFFFFFFFu, tk, 0)) {
+    tk = draw_ticket(J, kTicketReduce, lane);  // the next tile, read at the loop's end
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -612,8 +613,9 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
   uint32_t t_lo, t_hi;
   s2_range(J, t_lo, t_hi);
   const uint32_t max_depth = J.max_depth;
-  const uint32_t warps = gridDim.x * kS2Warps;
-  for (uint32_t t = t_lo + blockIdx.x * kS2Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
+  uint32_t tk = __shfl_sync(0xFFFFFFFFu, draw_ticket(J, kTicketBuild, lane), 0);
+  for (uint32_t t = t_lo + tk; t < t_hi; t = t_lo + __shfl_sync(0xFFFFFFFFu, tk, 0)) {
+    tk = draw_ticket(J, kTicketBuild, lane);  // the next tile, read at the loop's end
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -902,6 +904,8 @@ __global__ void __launch_bounds__(1024) setup_kernel(const Job *__restrict__ job
     J.counters[5] = s_carry;
     J.counters[6] = 0;
     J.counters[7] = s_carry;
+    J.counters[kTicketReduce] = 0;
+    J.counters[kTicketBuild] = 0;
   }
 }
 
@@ -935,6 +939,8 @@ __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, ui
   }
   J.counters[6] = lo;
   J.counters[7] = max(hi, lo);
+  J.counters[kTicketReduce] = 0;
+  J.counters[kTicketBuild] = 0;
 }
 
 // Per-document results (error precedence: capacity, empty, UTF-8, unclosed

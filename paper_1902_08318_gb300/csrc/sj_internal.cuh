@@ -104,10 +104,20 @@ struct Job {
 };
 
 // Tile ranges of the launches: stage-1 kernels work on tiles [counters[4],
-// counters[5]), stage-2 kernels on [counters[6], counters[7]).  A run over
+// counters[5]), stage-2 kernels on [counters[6], counters[7]) (counters[8]
+// and [9] are the tile tickets of two stage-2 passes).  A run over
 // resident input sets both to all tiles; a run over a host document that
 // arrives in chunks moves them forward chunk by chunk (chunk_range_kernel).
-constexpr int kCounters = 8;
+constexpr int kCounters = 12;
+constexpr int kTicketReduce = 8, kTicketBuild = 9;  // tile tickets of the stage-2 passes
+
+// Tiles are handed to warps in order by a ticket counter (reset before each
+// launch): a warp takes its next tile when it finishes one, so tiles of
+// uneven cost do not leave a tail of busy warps.  The next ticket is drawn
+// when a tile starts and read when it ends, which hides the atomic's latency.
+__device__ __forceinline__ uint32_t draw_ticket(const Job &J, int which, int lane) {
+  return lane == 0 ? atomicAdd(&J.counters[which], 1u) : 0u;
+}
 __device__ __forceinline__ void s1_range(const Job &J, uint32_t &lo, uint32_t &hi) {
   lo = J.counters[4];
   hi = J.counters[5];
