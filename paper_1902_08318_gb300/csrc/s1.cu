@@ -99,8 +99,10 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
   uint32_t *my_words = s_words[threadIdx.x];
   uint32_t t_lo, t_hi;
   s1_range(J, t_lo, t_hi);
-  const uint32_t warps = gridDim.x * kS1Warps;
-  for (uint32_t t = t_lo + blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
+  TileTickets tix(J, kTicketS1, t_lo, t_hi, blockIdx.x * kS1Warps + (threadIdx.x >> 5),
+                  gridDim.x * kS1Warps, lane);
+  for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
+    tix.draw();
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];

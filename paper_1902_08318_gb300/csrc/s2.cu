@@ -289,9 +289,10 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
     whead += m;
     __syncwarp();
   };
-  uint32_t tk = __shfl_sync(0xFFFFFFFFu, draw_ticket(J, kTicketReduce, lane), 0);
-  for (uint32_t t = t_lo + tk; t < t_hi; t = t_lo + __shfl_sync(0xFFFFFFFFu, tk, 0)) {
-    tk = draw_ticket(J, kTicketReduce, lane);  // the next tile, read at the loop's end
+  TileTickets tix(J, kTicketReduce, t_lo, t_hi, blockIdx.x * kS2Warps + wid, gridDim.x * kS2Warps,
+                  lane);
+  for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
+    tix.draw();  // the next tile, read at the loop's end
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -504,8 +505,10 @@ __global__ void __launch_bounds__(kNumThreads) numbers_kernel(const Job *__restr
   };
   uint32_t t_lo, t_hi;
   s2_range(J, t_lo, t_hi);
-  const uint32_t warps = gridDim.x * (kNumThreads / 32);
-  for (uint32_t t = t_lo + blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5); t < t_hi; t += warps) {
+  TileTickets tix(J, kTicketNumbers, t_lo, t_hi, blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5),
+                  gridDim.x * (kNumThreads / 32), lane);
+  for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
+    tix.draw();
     const uint32_t d = doc_of_tile(J, t);
     if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
     const uint32_t m = J.tile_nnum[t] & ~kTileHasEscapes;
@@ -613,9 +616,10 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
   uint32_t t_lo, t_hi;
   s2_range(J, t_lo, t_hi);
   const uint32_t max_depth = J.max_depth;
-  uint32_t tk = __shfl_sync(0xFFFFFFFFu, draw_ticket(J, kTicketBuild, lane), 0);
-  for (uint32_t t = t_lo + tk; t < t_hi; t = t_lo + __shfl_sync(0xFFFFFFFFu, tk, 0)) {
-    tk = draw_ticket(J, kTicketBuild, lane);  // the next tile, read at the loop's end
+  TileTickets tix(J, kTicketBuild, t_lo, t_hi, blockIdx.x * kS2Warps + (threadIdx.x >> 5),
+                  gridDim.x * kS2Warps, lane);
+  for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
+    tix.draw();  // the next tile, read at the loop's end
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     const uint32_t tt = t - j_min;
@@ -904,8 +908,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(const Job *__restrict__ job
     J.counters[5] = s_carry;
     J.counters[6] = 0;
     J.counters[7] = s_carry;
-    J.counters[kTicketReduce] = 0;
-    J.counters[kTicketBuild] = 0;
+    for (int k = kTicketReduce; k <= kTicketS1; k++) J.counters[k] = 0;
   }
 }
 
@@ -923,6 +926,7 @@ __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, ui
   if (!stage2) {
     J.counters[4] = min(lo1, J.counters[2]);
     J.counters[5] = min(hi1, J.counters[2]);
+    J.counters[kTicketS1] = 0;
     if (lo1 == 0) {  // the first chunk: no stage-2 tile is done yet
       J.counters[6] = 0;
       J.counters[7] = 0;
@@ -941,6 +945,7 @@ __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, ui
   J.counters[7] = max(hi, lo);
   J.counters[kTicketReduce] = 0;
   J.counters[kTicketBuild] = 0;
+  J.counters[kTicketNumbers] = 0;
 }
 
 // Per-document results (error precedence: capacity, empty, UTF-8, unclosed

@@ -270,11 +270,11 @@ __global__ void jump_kernel(const Job *__restrict__ job) {
 // each range with all lanes.
 __global__ void frontier_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  uint32_t lo, n;
-  s2_range(J, lo, n);
+  uint32_t t_lo, t_hi;
+  s2_range(J, t_lo, t_hi);
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
-  for (uint32_t t = lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < n; t += nw) {
+  for (uint32_t t = t_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < t_hi; t += nw) {
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t j_min = J.tile_first[d];
     if (J.doc_flags[d] & (kFlagUtf8 | kFlagUnclosed | kFlagCapacity)) continue;

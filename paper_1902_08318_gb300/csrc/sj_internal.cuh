@@ -105,19 +105,36 @@ struct Job {
 
 // Tile ranges of the launches: stage-1 kernels work on tiles [counters[4],
 // counters[5]), stage-2 kernels on [counters[6], counters[7]) (counters[8]
-// and [9] are the tile tickets of two stage-2 passes).  A run over
+// to [11] are the tile tickets of four passes).  A run over
 // resident input sets both to all tiles; a run over a host document that
 // arrives in chunks moves them forward chunk by chunk (chunk_range_kernel).
-constexpr int kCounters = 12;
-constexpr int kTicketReduce = 8, kTicketBuild = 9;  // tile tickets of the stage-2 passes
+constexpr int kCounters = 16;
+// tile tickets: stage-2 reduce, build and numbers; stage-1 blocks
+constexpr int kTicketReduce = 8, kTicketBuild = 9, kTicketNumbers = 10, kTicketS1 = 11;
 
-// Tiles are handed to warps in order by a ticket counter (reset before each
-// launch): a warp takes its next tile when it finishes one, so tiles of
-// uneven cost do not leave a tail of busy warps.  The next ticket is drawn
-// when a tile starts and read when it ends, which hides the atomic's latency.
-__device__ __forceinline__ uint32_t draw_ticket(const Job &J, int which, int lane) {
-  return lane == 0 ? atomicAdd(&J.counters[which], 1u) : 0u;
-}
+// Tiles of uneven cost: a warp takes its first tile by its index in the grid
+// and each later one from a ticket counter (reset before each launch) when it
+// finishes the previous, so no tail of busy warps is left.  The next ticket
+// is drawn when a tile starts and read when it ends, which hides the atomic's
+// latency; no ticket is drawn while no tile lies past the first round (small
+// inputs never touch the counter).  Usage:
+//   TileTickets tt(J, kTicket..., lo, hi, warp_in_grid, warps_in_grid, lane);
+//   for (uint32_t t = tt.first(); t < hi; t = tt.next()) { tt.draw(); ... }
+struct TileTickets {
+  uint32_t *ctr;
+  uint32_t past, first_t, hi, tk;
+  int lane;
+  __device__ TileTickets(const Job &J, int which, uint32_t lo, uint32_t hi_, uint32_t gw,
+                         uint32_t nw, int lane_)
+      : ctr(&J.counters[which]), past(lo + nw), first_t(lo + gw), hi(hi_), tk(0), lane(lane_) {}
+  __device__ __forceinline__ uint32_t first() const { return first_t; }
+  __device__ __forceinline__ void draw() {
+    tk = past < hi && lane == 0 ? atomicAdd(ctr, 1u) : 0u;
+  }
+  __device__ __forceinline__ uint32_t next() const {
+    return past + __shfl_sync(0xFFFFFFFFu, tk, 0);
+  }
+};
 __device__ __forceinline__ void s1_range(const Job &J, uint32_t &lo, uint32_t &hi) {
   lo = J.counters[4];
   hi = J.counters[5];
