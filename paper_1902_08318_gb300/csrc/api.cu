@@ -103,6 +103,8 @@ struct sj_parser {
   static constexpr uint32_t kMaxChunks = 64;
   uint64_t host_chunk = 512ull << 20;  // largest chunk; 0 = never chunk
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // the numbers kernel, beside the tile scan and frontier
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_start = nullptr;
   cudaEvent_t ev_chunk[kMaxChunks] = {};
   bool chunked_run = false;
@@ -138,6 +140,9 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
     if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
   if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
+  if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
+  if (p->ev_fork) cudaEventDestroy(p->ev_fork);
+  if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->ev_start) cudaEventDestroy(p->ev_start);
   for (cudaEvent_t e : p->ev_chunk)
     if (e) cudaEventDestroy(e);
@@ -211,6 +216,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
   CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
+  CK(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
@@ -315,16 +323,27 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[4], s);
 }
 
+// Stage 2.  The number conversions need only the reduce pass, and the tile
+// scan and frontier do not touch their data, so (except in profiled runs,
+// which time each stage alone) the numbers kernel runs on a second stream
+// beside the scan and frontier kernels, joined before the build pass.
 static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
+  if (!ev) {
+    cudaEventRecord(p->ev_fork, s);
+    cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
+    sj::numbers_kernel<<<p->num_grid, 128, 0, p->aux_stream>>>(p->d_job);
+    cudaEventRecord(p->ev_join, p->aux_stream);
+  }
   sj::launch_scan2(p->d_job, p->scan_grid, s);
   for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
     sj::spt_build_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job, src);
   sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
-  sj::numbers_kernel<<<p->num_grid, 128, 0, s>>>(p->d_job);
+  if (ev) sj::numbers_kernel<<<p->num_grid, 128, 0, s>>>(p->d_job);
+  else cudaStreamWaitEvent(s, p->ev_join, 0);
   if (ev) cudaEventRecord(ev[7], s);
   sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);
