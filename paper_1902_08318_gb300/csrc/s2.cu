@@ -633,6 +633,8 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
     uint64_t *tape = J.tape + tape_base(J, d);
     uint8_t *strs = J.strings + str_base(J, d);
     const uint64_t tape_cap = len + 3;
+    // tape indices of the chunk loop in 32 bits (documents stay below 2^32 - 256 bytes)
+    const uint32_t tape_cap32 = (uint32_t)min(tape_cap, (uint64_t)0xFFFFFFFFu);
     const uint64_t str_cap = str_base(J, d + 1) - str_base(J, d);
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
     const S2Pre pre = J.s2_pre[t];
@@ -758,7 +760,7 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
       const uint32_t sl = (valid && k == K_STRING) ? sl_all : 0u;
       const int32_t E = pre.d_start + ((int32_t)((meta >> 4) & 0x1FFFu) - 4096);
       const uint32_t trel = (uint32_t)(meta >> 17) & 0x1FFFu;
-      const uint64_t tp = (uint64_t)pre.tape_start + trel;
+      const uint32_t tp = pre.tape_start + trel;
       const uint32_t parent = (uint32_t)(meta >> 30) & 0xFFFFu;
       uint8_t p = __shfl_up_sync(0xFFFFFFFFu, k, 1);
       uint8_t pp = __shfl_up_sync(0xFFFFFFFFu, k, 2);
@@ -766,22 +768,22 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
       if (lane == 1) pp = prev1;
       prev2 = __shfl_sync(0xFFFFFFFFu, k, 30);
       prev1 = __shfl_sync(0xFFFFFFFFu, k, 31);
-      const uint64_t g = (uint64_t)off + j;
+      const uint32_t g = off + j;
 
       // ---- grammar: the enclosing container and the previous two tokens ----
       uint8_t K = 0;
-      uint64_t par_tape = ~0ull;
+      uint32_t par_tape = 0xFFFFFFFFu;
       bool par_ok = true;
       if (E >= 1) {
         if (parent) {
           K = (parent & 0x4000u) ? K_OPEN_OBJ : K_OPEN_ARR;
-          par_tape = (uint64_t)pre.tape_start + (parent & 0x0FFFu);
+          par_tape = pre.tape_start + (parent & 0x0FFFu);
         } else if (E >= max(1, pre.low) && E <= pre.d_start) {
           const uint32_t fk = (uint32_t)(pre.d_start - E);
           const uint64_t ent = fk < kFrontSmem ? W.front[fk] : front[fk];
           if (ent != ~0ull) {
             K = (ent >> 63) ? K_OPEN_OBJ : K_OPEN_ARR;
-            par_tape = ent & 0xFFFFFFFFull;
+            par_tape = (uint32_t)ent;
           } else {
             par_ok = false;
           }
@@ -806,14 +808,14 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
       // smaller than any content code, so the minimum keeps the grammar first.
       if (valid) {
         if (is_close(k)) {
-          if (!code && tp < tape_cap && par_tape < tape_cap) {
+          if (!code && tp < tape_cap32 && par_tape < tape_cap32) {
             tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
-            tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (tp + 1);
+            tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (uint64_t)(tp + 1);
           }
         } else if (k == K_NUMBER) {  // converted by the reduce pass (Sec. 3.2.1)
           if (sl_all & kSlenErr) {
             if (!code) code = (int)(sl_all & 0xFFu);
-          } else if (tp + 1 < tape_cap) {
+          } else if (tp < tape_cap32 - 1u) {  // tape_cap32 >= 3
             tape[tp] = (uint64_t)(sl_all & 0xFFu) << 56;
             tape[tp + 1] = nv;
           }
@@ -838,7 +840,7 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
             }
           }
           if (!ok) { if (!code) code = k == K_TRUE ? SJ_T_ATOM_ERROR : (k == K_FALSE ? SJ_F_ATOM_ERROR : SJ_N_ATOM_ERROR); }
-          else if (tp < tape_cap) tape[tp] = (uint64_t)(uint8_t)lit << 56;
+          else if (tp < tape_cap32) tape[tp] = (uint64_t)(uint8_t)lit << 56;
         }
         if (code) report(J, d, g, code);
       }
