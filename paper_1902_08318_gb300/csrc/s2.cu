@@ -83,6 +83,10 @@ struct Staged {
   int64_t sbase;        // document position of bytes[0]
   uint64_t slimit;      // first document position not staged
   const uint8_t *smem;
+  // 32-bit view for positions at or after the tile start (p >= sbase):
+  // bytes[(uint32_t)p - sb32] is position p while (uint32_t)p - sb32 < sn32
+  uint32_t sb32, sn32;
+  __device__ __forceinline__ uint32_t rel(uint32_t p) const { return p - sb32; }
   __device__ __forceinline__ uint8_t at(uint64_t p) const {
     return (p < slimit && (int64_t)p >= sbase) ? smem[p - sbase] : doc[p];
   }
@@ -110,6 +114,8 @@ __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc,
   v.sbase = (int64_t)t0 - (int64_t)(g0 - a0);
   v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
   v.smem = bytes;
+  v.sb32 = (uint32_t)v.sbase;
+  v.sn32 = (uint32_t)(send - a0);
   return v;
 }
 
@@ -134,6 +140,8 @@ __device__ __forceinline__ Staged stage_tile_async(uint8_t *bytes, const uint8_t
   v.sbase = (int64_t)t0 - (int64_t)(g0 - a0);
   v.slimit = (uint64_t)((int64_t)t0 + (int64_t)(send - g0));
   v.smem = bytes;
+  v.sb32 = (uint32_t)v.sbase;
+  v.sn32 = (uint32_t)(send - a0);
   return v;
 }
 __device__ __forceinline__ void wait_staged() {
@@ -226,9 +234,9 @@ struct OpenTable {
 // Normalised length of a string without escapes or control bytes, from the
 // staged masks: the distance from its first content byte (document position
 // p0) to the next real quote.  False when the masks cannot decide it.
-__device__ __forceinline__ bool plain_string_len(const ReduceSmem &W, uint64_t t0, uint64_t p0,
+__device__ __forceinline__ bool plain_string_len(const ReduceSmem &W, uint32_t t0, uint32_t p0,
                                                  uint32_t nblk, uint32_t &L) {
-  const uint32_t rel = (uint32_t)(p0 - t0);
+  const uint32_t rel = p0 - t0;
   uint32_t w = rel >> 6, b = rel & 63, acc = 0;
   while (w < nblk) {
     const uint64_t q = W.q[w] >> b, x = W.x[w] >> b;
@@ -337,7 +345,7 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
       RQEntry e{0, 0, 0};
       if (have) e = W.sq[(shead + lane) & (kQueue - 1)];
       uint32_t L = 0;
-      const bool ok = have && plain_string_len(W, t0, (uint64_t)e.pos + 1, nblk, L);
+      const bool ok = have && plain_string_len(W, (uint32_t)t0, e.pos + 1, nblk, L);
       if (ok) {
         slen[e.j] = L;
         sb += 5u + L;
@@ -357,7 +365,7 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
       const bool valid = j < cnt;
       uint32_t pos, nxt;
       ps.next(pos, nxt, idxp, off, cnt, nidx, len, base, lane);
-      const uint8_t kind = valid ? s_kind[sv.smem[pos - sv.sbase]] : K_OTHER;
+      const uint8_t kind = valid ? s_kind[sv.smem[sv.rel(pos)]] : K_OTHER;
       // depth and tape slot: one scan over (delta + 1) | words << 8
       const int32_t dl = depth_delta(kind);
       const uint32_t w = tape_words_of(kind);
