@@ -192,7 +192,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
-  if ((r = dalloc(p, &p->d_unesc, max_bytes + 64))) return r;
+  if ((r = dalloc(p, &p->d_unesc, max_bytes + 64 + 16))) return r;
   if ((r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_nlist, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_tile_nnum, tiles))) return r;
@@ -497,6 +497,9 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
   }
   p->h_job->base = base;
   p->h_job->src = src;
+  // the scratch copy of escaped strings keeps the input's alignment modulo 16
+  // (the build pass stages both windows alike)
+  p->h_job->unesc = p->d_unesc + (((uintptr_t)base + p->h_doc_off[0]) & 15u);
   p->h_job->n_docs = n_docs;
   p->chunked_run = chunked;
   if (chunked) {

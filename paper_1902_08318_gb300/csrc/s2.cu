@@ -668,10 +668,12 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
     const Staged sv = stage_tile<kStageBytesB>(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
     uint32_t shead = 0, stail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
-    // the scratch window, copied ahead when the tile has strings with escapes
-    const bool has_esc = (J.tile_nnum[t] & kTileHasEscapes) != 0;
-    Staged us{};
-    if (has_esc) us = stage_tile_async<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
+    // the scratch window, copied ahead when the tile has strings with escapes.
+    // The scratch buffer has the input's alignment modulo 16, so the window
+    // covers the same positions as the staged input (sv) in W.ubytes.
+    const bool has_esc = (J.tile_nnum[t] & kTileHasEscapes) != 0 &&
+                         (((uintptr_t)unesc ^ (uintptr_t)doc) & 15u) == 0;
+    if (has_esc) stage_tile_async<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
     bool us_ready = !has_esc;
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
@@ -706,8 +708,7 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
         wait_staged();
         us_ready = true;
       }
-      const Staged &src = walk ? us : sv;
-      const bool fits = !is_str || (n < kSlenLen && p0 + n <= src.slimit);
+      const bool fits = !is_str || (n < kSlenLen && p0 + n <= sv.slimit && (!walk || has_esc));
       const unsigned sm = __ballot_sync(0xFFFFFFFFu, is_str);
       if (sm) {
         const bool all_fit = __all_sync(0xFFFFFFFFu, fits);
@@ -716,7 +717,8 @@ __global__ void __launch_bounds__(kS2Threads, 6) stage2_build_kernel(const Job *
         const uint32_t a = (uint32_t)((uintptr_t)(strs + so_lo) & 15u);
         const uint64_t total = a + (so_hi - so_lo);
         if (all_fit && total <= (uint64_t)kStrStage && so_hi <= str_cap) {
-          if (is_str) put_string_smem(W.sout + a + (so - so_lo), (uint32_t)n, src.smem + (p0 - src.sbase));
+          if (is_str)
+            put_string_smem(W.sout + a + (so - so_lo), (uint32_t)n, (walk ? W.ubytes : W.bytes) + (p0 - sv.sbase));
           __syncwarp();
           uint8_t *gb = strs + so_lo - a;  // 16-byte aligned
           const uint32_t units = (uint32_t)((total + 15) >> 4);
