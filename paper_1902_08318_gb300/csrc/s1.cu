@@ -213,18 +213,32 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
 // memory so that the stores are coalesced.
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ uint32_t stage[kS1Warps][kTileBytes];
+  __shared__ uint16_t stage[kS1Warps][kTileBytes];  // tile-relative positions
   const int lane = threadIdx.x & 31;
-  uint32_t *out_stage = stage[threadIdx.x >> 5];
+  uint16_t *out_stage = stage[threadIdx.x >> 5];
   uint32_t t_lo, t_hi;
   s1_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * kS1Warps;
-  for (uint32_t t = t_lo + blockIdx.x * kS1Warps + (threadIdx.x >> 5); t < t_hi; t += warps) {
+  const ulonglong2 *blk = reinterpret_cast<const ulonglong2 *>(J.s1_blk);
+  // software pipeline: a tile's masks and prefix are loaded while the tile
+  // before it is written
+  uint32_t t = t_lo + blockIdx.x * kS1Warps + (threadIdx.x >> 5);
+  ulonglong2 v_next = make_ulonglong2(0, 0);
+  S1Pre pre_next{0, 0};
+  if (t < t_hi) {
+    v_next = blk[(uint64_t)t * 32 + lane];
+    pre_next = J.s1_pre[t];
+  }
+  for (; t < t_hi; t += warps) {
+    const ulonglong2 v = v_next;
+    const S1Pre pre = pre_next;
+    if (t + warps < t_hi) {
+      v_next = blk[(uint64_t)(t + warps) * 32 + lane];
+      pre_next = J.s1_pre[t + warps];
+    }
     const uint32_t d = doc_of_tile(J, t);
     const uint32_t tt = t - J.tile_first[d];
     const uint32_t ntiles_d = J.tile_first[d + 1] - J.tile_first[d];
-    const S1Pre pre = J.s1_pre[t];
-    const ulonglong2 v = reinterpret_cast<const ulonglong2 *>(J.s1_blk)[(uint64_t)t * 32 + lane];
     const uint64_t S = pre.q_in ? v.y : v.x;
     const uint32_t c = __popcll(S);
     uint32_t incl = c;
@@ -236,14 +250,15 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job
     const uint32_t n = __shfl_sync(0xFFFFFFFFu, incl, 31);
     uint32_t o = incl - c;
     uint64_t s = S;
-    const uint32_t pos0 = tt * kTileBytes + lane * kBlockBytes;
+    const uint32_t rel0 = lane * kBlockBytes;
     while (s) {
-      out_stage[o++] = pos0 + (uint32_t)(__ffsll((long long)s) - 1);
+      out_stage[o++] = (uint16_t)(rel0 + (uint32_t)(__ffsll((long long)s) - 1));
       s &= s - 1;
     }
     __syncwarp();
     uint32_t *dst = J.idx + idx_base(J, d) + pre.base;
-    for (uint32_t k = lane; k < n; k += 32) dst[k] = out_stage[k];
+    const uint32_t t0 = tt * kTileBytes;
+    for (uint32_t k = lane; k < n; k += 32) dst[k] = t0 + out_stage[k];
     __syncwarp();
     if (lane == 0) {
       J.tile_cnt[t] = n;
