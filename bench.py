@@ -191,6 +191,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     torch.cuda.set_device(dev)
     desc, size = WORKLOADS[args.workload]
     doc = make_doc(args.workload, 2000 + rank, size=(args.doc_mb << 20) if args.doc_mb else None)
+    if args.doc_mb and args.workload == "config2":  # a smaller document of the same recipe
+        desc = desc.replace("1 GiB single document", f"{args.doc_mb} MiB single document")
     B = int(doc.size)
     doc_dev = torch.from_numpy(doc).to(dev)
     parser = sj.Parser(max_bytes=B + 64)
