@@ -474,30 +474,41 @@ def query_leg(args, dev) -> dict:
 
 def serving_leg(args) -> dict:
     """Serving (config4): the arrival trace replayed natively against the
-    continuous-batching server (latency = result seen minus arrival)."""
+    continuous-batching server (latency = result seen minus arrival).  The
+    timed replay runs three times; the line reports the run with the median
+    p99 and lists every run's p50, p99 and maximum (the host is shared: a
+    replay now and then meets a stall of the polling thread)."""
     import gen
     import paper_1902_08318_gb300 as sj
     arrival, buf, off = gen.config4(workers=max(1, min(16, os.cpu_count() or 1)))
     n = arrival.size
     srv = sj.Server(max_batch_bytes=16 << 20, max_batch_docs=4096, max_slots=8,
                     mem_budget=8 << 30)
-    # warm-up: a slice of the trace (captures the graphs of every batch size)
+    # warm-up: a slice of the trace (the graphs of every batch size are
+    # captured when the server is created)
     w = 20_000
     srv.replay(buf, off[: w + 1], arrival[:w] - arrival[0])
-    b0 = srv.batches
-    lat, wall = srv.replay(buf, off, arrival)
-    batches = srv.batches - b0
+    runs = []
+    for _ in range(3):
+        b0 = srv.batches
+        lat, wall = srv.replay(buf, off, arrival)
+        runs.append({"p50": pct(lat, 50) * 1e3, "p99": pct(lat, 99) * 1e3,
+                     "max": float(lat.max()) * 1e3, "wall": wall, "batches": srv.batches - b0})
+    med = sorted(runs, key=lambda r: r["p99"])[1]
+    wall, batches = med["wall"], med["batches"]
     return {
         "workload": "config4: 200,000 requests, Poisson arrivals at 50,000/s, log-normal sizes "
                     "(median 4 KB, sigma 2, 64 B - 8 MB), 60% records / 25% number-heavy / "
                     "15% string-heavy",
         "requests": int(n), "bytes": int(off[-1]), "offered_req_per_s": round(n / float(arrival[-1]), 1),
         "docs_per_s": round(n / wall, 1), "GB_per_s": round(int(off[-1]) / wall / 1e9, 3),
-        "latency_ms_p50": round(pct(lat, 50) * 1e3, 4), "latency_ms_p99": round(pct(lat, 99) * 1e3, 4),
-        "latency_ms_max": round(float(lat.max()) * 1e3, 3),
+        "latency_ms_p50": round(med["p50"], 4), "latency_ms_p99": round(med["p99"], 4),
+        "latency_ms_max": round(med["max"], 3),
+        "runs_ms": [{k: round(r[k], 3) for k in ("p50", "p99", "max")} for r in runs],
         "slots": srv.slots, "device_bytes": srv.device_bytes, "mem_budget": 8 << 30,
         "batches": int(batches), "docs_per_batch": round(n / max(1, batches), 2),
-        "timing": "host clock; arrival = scheduled time, done = result seen by the polling loop",
+        "timing": "host clock; arrival = scheduled time, done = result seen by the polling loop; "
+                  "the run with the median p99 of three timed replays",
     }
 
 

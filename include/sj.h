@@ -227,6 +227,13 @@ sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
  * or host input that is not chunked). */
 int sj_parser_kernels_per_run(const sj_parser *p);
 
+/* Capture now the runs (CUDA graphs) of every batch size up to max_docs
+ * documents (0 = the parser's max_docs), which are otherwise captured on the
+ * first run of each size (one graph per power-of-two bucket of document
+ * counts).  A server calls it once per parser so that no capture happens
+ * while requests wait. */
+sj_status sj_parser_prepare(sj_parser *p, uint32_t max_docs);
+
 /* Host documents that arrive in chunks.  A single document in pinned host
  * memory (cudaMallocHost / cudaHostRegister) longer than chunk_bytes is
  * parsed while it is copied: a second stream copies it chunk by chunk, and

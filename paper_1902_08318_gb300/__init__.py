@@ -136,6 +136,8 @@ def load(path: str | None = None):
     lib.sj_parser_stage_times.restype = ctypes.c_int
     lib.sj_parser_kernels_per_run.argtypes = [vp]
     lib.sj_parser_kernels_per_run.restype = ctypes.c_int
+    lib.sj_parser_prepare.argtypes = [vp, u32]
+    lib.sj_parser_prepare.restype = ctypes.c_int
     lib.sj_parser_set_host_chunk.argtypes = [vp, u64]
     lib.sj_parser_set_host_chunk.restype = ctypes.c_int
     lib.sj_stage1_indices_noalloc.argtypes = [vp, u64, vp, vp, vp]
@@ -199,7 +201,7 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay",
             "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune",
             "sj_query_create", "sj_query_destroy", "sj_query_distinct",
-            "sj_parser_set_host_chunk"]
+            "sj_parser_set_host_chunk", "sj_parser_prepare"]
 TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
 STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
           "s2_numbers", "s2_build", "finalize")
@@ -347,6 +349,10 @@ class Parser:
 
     def kernels_per_run(self) -> int:
         return int(self._lib.sj_parser_kernels_per_run(self._h))
+
+    def prepare(self, max_docs: int = 0):
+        """Capture the runs of every batch size up to max_docs now."""
+        _check(self._lib.sj_parser_prepare(self._h, int(max_docs)))
 
     def set_host_chunk(self, chunk_bytes: int):
         """Chunk size for single documents in pinned host memory, parsed while

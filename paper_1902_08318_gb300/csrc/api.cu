@@ -642,6 +642,18 @@ extern "C" sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n) {
   return SJ_SUCCESS;
 }
 
+extern "C" sj_status sj_parser_prepare(sj_parser *p, uint32_t max_docs) {
+  if (!p) return SJ_INVALID_ARG;
+  if (max_docs == 0 || max_docs > p->max_docs) max_docs = p->max_docs;
+  for (uint64_t n = 1;; n <<= 1) {  // one graph per bucket (powers of two)
+    cudaGraphExec_t g;
+    const int r = ensure_graph(p, (uint32_t)(n < max_docs ? n : max_docs), &g);
+    if (r) return r;
+    if (n >= max_docs) break;
+  }
+  return SJ_SUCCESS;
+}
+
 extern "C" sj_status sj_parser_set_host_chunk(sj_parser *p, uint64_t chunk_bytes) {
   if (!p) return SJ_INVALID_ARG;
   int r;

@@ -107,6 +107,13 @@ extern "C" sj_status sj_server_create(sj_server **out, const sj_server_config *c
       sj_server_destroy(s);
       return SJ_MEMALLOC;
     }
+    // every batch size's run captured now, not on the first batch of that size
+    // while requests wait
+    if ((r = sj_parser_prepare(sl.p, s->cfg.max_batch_docs))) {
+      destroy_slot(sl);
+      sj_server_destroy(s);
+      return r;
+    }
     sl.offsets.reserve((size_t)s->cfg.max_batch_docs + 1);
     sl.tickets.reserve(s->cfg.max_batch_docs);
     sl.results.resize(s->cfg.max_batch_docs);
