@@ -44,3 +44,20 @@ def test_autotune_picks_valid_shapes_and_keeps_results():
         assert cur[k][0] == rep[k]["blocks_per_sm"]
         assert rep[k]["ms"] > 0
     gpuutil.compare(_outputs(p, doc), before, "after autotune")
+
+
+def test_prepare_then_batches_of_every_size():
+    # sj_parser_prepare captures the run of every batch-size bucket up front;
+    # later batches of any size (up to max_docs) replay them
+    import oracle
+    import paper_1902_08318_gb300 as sj
+    p = sj.Parser(max_bytes=1 << 20, max_docs=40)
+    p.prepare()
+    p.prepare(8)  # again, and a smaller bound: nothing to capture
+    pool = [b'{"a": [1, 2.5, "x"]}', b"[true, null, -0]", b'"s\\n"', b"[1,", b"tru",
+            gen.config0(7).tobytes()[:3000]]
+    for n in (1, 2, 3, 17, 40):
+        docs = [pool[i % len(pool)] for i in range(n)]
+        buf, off = gpuutil.batch_arrays(docs)
+        res, _ = p.parse_batch(buf, off)
+        assert [int(e) for e in res["error"]] == [oracle.parse(d)["error"] for d in docs]
