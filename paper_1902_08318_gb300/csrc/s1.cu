@@ -31,40 +31,44 @@ __device__ __forceinline__ uint64_t bs_run_before(const uint8_t *doc, uint64_t e
 }
 
 // UTF-8 check of one 64-byte block (Sec. 3.1.5, Table "tab:unicode").
-// The structure of the sequences is checked on bit masks: the continuation
-// bytes (10xxxxxx) must be exactly the positions that the lead bytes before
-// them require -- one after every 11xxxxxx lead, a second after 111xxxxx, a
-// third after 1111xxxx -- including positions required by leads among the 3
-// bytes before the block (`prev`, top bytes; missing bytes are 0).  The
-// remaining rules of the table concern single values (C0, C1 and F5-FF never
-// occur; after E0, ED, F0 and F4 the next byte has a narrower range) and are
-// checked at each lead byte, read from the block's copy `wb` in shared
-// memory.  A lead whose sequence runs past the block is checked by the next
-// block through its `prev`, or here when the document ends with the block.
+// The structure of the sequences is checked on per-byte flags (bit 7 of each
+// byte of a word): the continuation bytes (10xxxxxx) must be exactly the
+// positions that the lead bytes before them require -- one after every
+// 11xxxxxx lead, a second after 111xxxxx, a third after 1111xxxx -- including
+// positions required by leads among the 3 bytes before the block (`prev`, top
+// bytes; missing bytes are 0).  A word's required positions are its lead
+// flags moved up by one, two and three bytes, with the flags of the word
+// before shifted in.  The remaining rules of the table concern single values
+// (C0, C1 and F5-FF never occur; after E0, ED, F0 and F4 the next byte has a
+// narrower range) and are checked at each lead byte, read from the block's
+// copy `wb` in shared memory.  A lead whose sequence runs past the block is
+// checked by the next block through its `prev`, or here when the document
+// ends with the block.
 __device__ __forceinline__ bool utf8_block_error_masks(const uint32_t (&w)[16], const uint8_t *wb,
                                                  uint32_t prev, bool doc_ends_here) {
-  uint32_t cm[2] = {0, 0}, lm[2] = {0, 0}, l3[2] = {0, 0}, l4[2] = {0, 0};
+  // lead flags of the word before: >= 2-, >= 3- and 4-byte leads
+  uint32_t p2 = prev & (prev << 1) & 0x80808080u;
+  uint32_t p3 = p2 & (prev << 2), p4 = p3 & (prev << 3);
+  uint32_t bad = 0;
+  uint32_t lm[2] = {0, 0};
 #pragma unroll
   for (int j = 0; j < 16; j++) {
-    const uint32_t x = w[j], x1 = x << 1, x2 = x << 2, x3 = x << 3, t = x & x1;
-    const int h = j >> 3, sh = (j & 7) * 4;
-    cm[h] |= movemask4(x & ~x1 & 0x80808080u) << sh;
-    lm[h] |= movemask4(t & 0x80808080u) << sh;
-    l3[h] |= movemask4(t & x2 & 0x80808080u) << sh;
-    l4[h] |= movemask4(t & x2 & x3 & 0x80808080u) << sh;
+    const uint32_t x = w[j], x1 = x << 1;
+    const uint32_t c = x & ~x1 & 0x80808080u;  // continuation bytes
+    const uint32_t t2 = x & x1 & 0x80808080u;  // lead bytes
+    const uint32_t t3 = t2 & (x << 2), t4 = t3 & (x << 3);
+    const uint32_t req = __funnelshift_l(p2, t2, 8) | __funnelshift_l(p3, t3, 16) |
+                         __funnelshift_l(p4, t4, 24);
+    bad |= req ^ c;
+    lm[j >> 3] |= movemask4(t2) << ((j & 7) * 4);
+    p2 = t2;
+    p3 = t3;
+    p4 = t4;
   }
-  const uint64_t C = ((uint64_t)cm[1] << 32) | cm[0], L = ((uint64_t)lm[1] << 32) | lm[0];
-  const uint64_t L3 = ((uint64_t)l3[1] << 32) | l3[0], L4 = ((uint64_t)l4[1] << 32) | l4[0];
-  // leads among the bytes before the block (bit 3 = byte -1, 2 = -2, 1 = -3)
-  const uint32_t pt = prev & (prev << 1);
-  const uint32_t pl = movemask4(pt & 0x80808080u), pl3 = movemask4(pt & (prev << 2) & 0x80808080u);
-  const uint32_t pl4 = movemask4(pt & (prev << 2) & (prev << 3) & 0x80808080u);
-  const uint64_t req_in = ((pl >> 3) & 1u) | ((pl3 >> 2) & 2u) | ((pl4 >> 1) & 4u) |  // lead at -1
-                          ((pl3 >> 2) & 1u) | ((pl4 >> 1) & 2u) |                    // lead at -2
-                          ((pl4 >> 1) & 1u);                                         // lead at -3
-  const uint64_t REQ = (L << 1) | (L3 << 2) | (L4 << 3) | req_in;
-  if (C != REQ) return true;
-  if (doc_ends_here && ((L >> 63) | (L3 >> 62) | (L4 >> 61))) return true;
+  if (bad) return true;
+  // leads in the last bytes whose sequences run past the document's end
+  if (doc_ends_here && ((p2 & 0x80000000u) | (p3 & 0x80800000u) | (p4 & 0x80808000u))) return true;
+  const uint64_t L = ((uint64_t)lm[1] << 32) | lm[0];
   // value rules
   const uint32_t pb = prev >> 24;  // byte -1
   if (pb == 0xE0 || pb == 0xED || pb == 0xF0 || pb == 0xF4) {
