@@ -84,34 +84,41 @@ def load_peaks() -> dict:
     return {"hbm_gbs": 6800.0, "source": "fallback"}
 
 
-# The files that define the profiled kernels (stage 1, tile scans and
-# frontier, stage 2 with numbers); host-side code (api.cu, server.cpp, the
-# query and the allocation-free entry) does not change their DRAM traffic.
-KERNEL_SOURCES = ("s1.cu", "s1_common.cuh", "scan.cu", "s2.cu", "strings.cuh", "number.cuh",
-                  "pow5_table.h", "sj_internal.cuh")
+# The files that define each profiled kernel; host-side code (api.cu,
+# server.cpp, the query and the allocation-free entry) does not change their
+# DRAM traffic, and neither does a change to another stage's kernel.
+_S1 = ("s1.cu", "s1_common.cuh", "sj_internal.cuh")
+_S2 = ("s2.cu", "strings.cuh", "number.cuh", "pow5_table.h", "sj_internal.cuh")
+KERNEL_SOURCES = {"s1_blocks": _S1, "s1_flatten": _S1, "s2_reduce": _S2, "s2_numbers": _S2,
+                  "s2_build": _S2}
 
 
-def source_hash() -> str:
-    h = hashlib.sha256()
+def source_hash(kernel: str, read=None) -> str:
+    """Hash of the sources of one kernel (`read(name)` gives a file's bytes;
+    by default the working tree)."""
     csrc = os.path.join(ROOT, "paper_1902_08318_gb300", "csrc")
-    for name in KERNEL_SOURCES:
-        with open(os.path.join(csrc, name), "rb") as f:
-            h.update(name.encode() + f.read())
+    if read is None:
+        def read(name):
+            with open(os.path.join(csrc, name), "rb") as f:
+                return f.read()
+    h = hashlib.sha256()
+    for name in KERNEL_SOURCES[kernel]:
+        h.update(name.encode() + read(name))
     return h.hexdigest()[:16]
 
 
 def ncu_traffic(kernel: str):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel sources."""
+    on the kernel's current sources."""
     p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    if not os.path.exists(p):
+    if not os.path.exists(p) or kernel not in KERNEL_SOURCES:
         return None
     with open(p) as f:
         d = json.load(f)
-    if d.get("source_hash") != source_hash():
-        return None
     ent = d.get("kernels", {}).get(kernel)
     if not ent or "bytes_per_launch_full_size" not in ent:
+        return None
+    if ent.get("source_hash") != source_hash(kernel):
         return None
     return ent["bytes_per_launch_full_size"]
 
