@@ -97,3 +97,19 @@ def test_many_chunks_are_merged(parser):
     parser.set_host_chunk(K)  # 63 chunks of one tile, then 450 tiles
     gpuutil.compare(gpuutil.gpu_result(parser, _pinned(d)), oracle.parse(d), "merged chunks")
     parser.set_host_chunk(512 << 20)
+
+
+def test_chunks_spanning_several_scan_blocks():
+    # a tile scan covers 1024 tiles (2 MiB) per block: with a largest chunk of
+    # 6 MiB the later chunks span several scan blocks, each scan starting from
+    # the carry of the chunk before
+    import paper_1902_08318_gb300 as sj
+    d = gen.config2(2011, size=(20 << 20) + 1234).tobytes()
+    p = sj.Parser(max_bytes=len(d) + 64)
+    ref = gpuutil.gpu_result(p, torch.frombuffer(bytearray(d), dtype=torch.uint8).cuda())
+    for chunk in (6 << 20, (3 << 20) + 2048):
+        p.set_host_chunk(chunk)
+        got = gpuutil.gpu_result(p, _pinned(d, shift=5))
+        gpuutil.compare(got, ref, f"chunk {chunk}: chunked vs device")
+    gpuutil.compare(ref, oracle.parse(d), "device vs oracle")
+    p.close()
