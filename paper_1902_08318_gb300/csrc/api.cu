@@ -30,8 +30,8 @@ __global__ void finalize_kernel(const Job *job);
 __global__ void spt_build_kernel(const Job *job, uint32_t src);
 __global__ void jump_kernel(const Job *job);
 __global__ void frontier_kernel(const Job *job);
-__global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, int stage2,
-                                   int last);
+__global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, int mode,
+                                   uint32_t c, int last);
 void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
 void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
 }  // namespace sj
@@ -60,6 +60,8 @@ struct sj_parser {
   sj::S2Pre *d_s2_pre = nullptr;
   sj::S2Agg *d_scan_agg = nullptr;
   sj::S2Agg *d_scan_pre = nullptr;
+  sj::S1Agg *d_scan_agg1 = nullptr;
+  sj::S1Agg *d_scan_pre1 = nullptr;
   int32_t *d_spt = nullptr;
   uint32_t *d_slen = nullptr;
   ulonglong2 *d_s1_qx = nullptr;
@@ -101,12 +103,16 @@ struct sj_parser {
   cudaEvent_t prof[kStages + 1] = {};
   // chunked runs over a host document
   static constexpr uint32_t kMaxChunks = 64;
+  static_assert(kMaxChunks <= (uint32_t)sj::kMaxChunkSlots, "a stage-2 bound slot per chunk");
   uint64_t host_chunk = 512ull << 20;  // largest chunk; 0 = never chunk
   cudaStream_t copy_stream = nullptr;
   cudaStream_t aux_stream = nullptr;  // the numbers kernel, beside the tile scan and frontier
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_start = nullptr;
   cudaEvent_t ev_chunk[kMaxChunks] = {};
+  cudaStream_t s1_stream = nullptr;  // stage 1 of the chunks, ahead of stage 2
+  cudaEvent_t ev_setup = nullptr;
+  cudaEvent_t ev_s1[kMaxChunks] = {};
   bool chunked_run = false;
   bool profiling = false;
   bool profiled_run = false;
@@ -144,6 +150,10 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
   if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->s1_stream) cudaStreamDestroy(p->s1_stream);
+  if (p->ev_setup) cudaEventDestroy(p->ev_setup);
+  for (cudaEvent_t e : p->ev_s1)
+    if (e) cudaEventDestroy(e);
   for (cudaEvent_t e : p->ev_chunk)
     if (e) cudaEventDestroy(e);
   if (p->done) cudaEventDestroy(p->done);
@@ -151,7 +161,7 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
     if (e) cudaEventDestroy(e);
   void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_tile_cnt,
                  p->d_tile_off, p->d_s1_rec, p->d_s1_pre, p->d_s1_blk, p->d_s2_rec, p->d_s2_pre,
-                 p->d_scan_agg, p->d_scan_pre, p->d_spt, p->d_slen, p->d_front, p->d_surv,
+                 p->d_scan_agg, p->d_scan_pre, p->d_scan_agg1, p->d_scan_pre1, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
                  p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
                  p->d_open_g, p->d_unesc, p->d_numv, p->d_nlist, p->d_tile_nnum};
@@ -188,6 +198,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_s2_pre, tiles))) return r;
   if ((r = dalloc(p, &p->d_scan_agg, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_scan_pre, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_agg1, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_pre1, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
   if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
@@ -221,6 +233,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&p->s1_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->ev_setup, cudaEventDisableTiming));
+  for (cudaEvent_t &e : p->ev_s1) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
 
   int sms = 0, occ1 = 0, occf = 0, occ2r = 0, occ2b = 0;
   CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
@@ -269,6 +284,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.s2_pre = p->d_s2_pre;
   J.scan_agg = p->d_scan_agg;
   J.scan_pre = p->d_scan_pre;
+  J.scan_agg1 = p->d_scan_agg1;
+  J.scan_pre1 = p->d_scan_pre1;
   J.spt = p->d_spt;
   J.spt_stride = (uint32_t)tiles;
   J.spt_levels = p->spt_levels;
@@ -432,10 +449,12 @@ static int wait_pending(sj_parser *p) {
 
 // One document of `len` bytes in pinned host memory, parsed while it is copied
 // (Sec. 3: stage 1 and stage 2 may run over a stream of chunks).  The copy
-// stream moves the chunks in order, each followed by an event; the run's
+// stream moves the chunks in order, each followed by an event; a stage-1
 // stream waits for chunk c, runs stage 1 on its tiles (the tile scans carry
-// the state of the tiles before), then stage 2 on the tiles the device found
-// ready (chunk_range_kernel), and after the last chunk on all that remain.
+// the state of the tiles before) and notes the stage-2 bound the chunk
+// allows; the run's stream waits for that, runs stage 2 on the tiles up to
+// the bound (chunk_range_kernel), and after the last chunk on all that
+// remain.
 static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cudaStream_t s) {
   // Chunk sizes: a small first chunk (nothing overlaps its copy), then
   // doubling up to host_chunk; the copies run about twice as fast as the
@@ -464,12 +483,22 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
     CK(cudaEventRecord(p->ev_chunk[c], p->copy_stream));
   }
   sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  // stage 1 of every chunk on its own stream, as the chunks land: it reads
+  // landed bytes and writes the arrays of its own tiles only (its tile scan
+  // has its own scratch), so it runs beside stage 2 of the chunks before
+  CK(cudaEventRecord(p->ev_setup, s));
+  CK(cudaStreamWaitEvent(p->s1_stream, p->ev_setup, 0));
   for (uint32_t c = 0; c < nc; c++) {
-    CK(cudaStreamWaitEvent(s, p->ev_chunk[c], 0));
-    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, (uint32_t)(at[c] / tile),
-                                            (uint32_t)((at[c + 1] + tile - 1) / tile), 0, 0);
-    enqueue_stage1(p, s, nullptr);
-    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 1, c + 1 == nc);
+    CK(cudaStreamWaitEvent(p->s1_stream, p->ev_chunk[c], 0));
+    sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(
+        p->d_job, (uint32_t)(at[c] / tile), (uint32_t)((at[c + 1] + tile - 1) / tile), 0, c, 0);
+    enqueue_stage1(p, p->s1_stream, nullptr);
+    sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(p->d_job, 0, 0, 1, c, 0);
+    CK(cudaEventRecord(p->ev_s1[c], p->s1_stream));
+  }
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaStreamWaitEvent(s, p->ev_s1[c], 0));
+    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
     enqueue_stage2(p, s, nullptr);
   }
   sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);

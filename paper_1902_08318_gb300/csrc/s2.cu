@@ -924,18 +924,22 @@ __global__ void __launch_bounds__(1024) setup_kernel(const Job *__restrict__ job
   }
 }
 
-// A document that arrives in chunks (one document; host input): the tiles of
-// the next stage-1 launches are [lo1, hi1).  With `stage2`, the tiles of the
-// next stage-2 launches start where the previous ones stopped and end before
-// the tile holding the last index found so far: each token of those tiles is
-// followed by a known index, so its bytes, and the staged bytes and masks
-// after its tile, lie in chunks that have arrived and passed stage 1.  With
-// `last` they run to the end of the document.
+// A document that arrives in chunks (one document; host input).
+//   mode 0: the tiles of the next stage-1 launches are [lo1, hi1);
+//   mode 1 (after stage 1 of chunk c, on the same stream): the stage-2 bound
+//     that chunk allows, kept in chunk c's slot: the tile holding the last
+//     index found so far -- every token of the tiles before it is followed by
+//     a known index, so its bytes, and the staged bytes and masks after its
+//     tile, lie in chunks that have landed and passed stage 1;
+//   mode 2: the tiles of the next stage-2 launches: from where the previous
+//     ones stopped to chunk c's bound, or with `last` to the document's end.
+// The bound is taken in mode 1 because stage 1 of later chunks runs on
+// another stream meanwhile and moves the running index count.
 __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, uint32_t hi1,
-                                   int stage2, int last) {
+                                   int mode, uint32_t c, int last) {
   const Job &J = *job;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  if (!stage2) {
+  if (mode == 0) {
     J.counters[4] = min(lo1, J.counters[2]);
     J.counters[5] = min(hi1, J.counters[2]);
     J.counters[kTicketS1] = 0;
@@ -945,14 +949,17 @@ __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, ui
     }
     return;
   }
-  const uint32_t lo = J.counters[7];
-  uint32_t hi = lo;
-  if (last) {
-    hi = J.counters[2];
-  } else if (J.n_docs == 1 && !(J.doc_flags[0] & kDocBad)) {
-    const uint32_t n = J.doc_nidx[0];
-    if (n) hi = J.tile_first[0] + J.idx[idx_base(J, 0) + n - 1] / (uint32_t)kTileBytes;
+  if (mode == 1) {
+    uint32_t hi = 0;
+    if (J.n_docs == 1 && !(J.doc_flags[0] & kDocBad)) {
+      const uint32_t n = J.doc_nidx[0];
+      if (n) hi = J.tile_first[0] + J.idx[idx_base(J, 0) + n - 1] / (uint32_t)kTileBytes;
+    }
+    J.counters[kChunkSlots + min(c, (uint32_t)kMaxChunkSlots - 1u)] = hi;
+    return;
   }
+  const uint32_t lo = J.counters[7];
+  const uint32_t hi = last ? J.counters[2] : J.counters[kChunkSlots + min(c, (uint32_t)kMaxChunkSlots - 1u)];
   J.counters[6] = lo;
   J.counters[7] = max(hi, lo);
   J.counters[kTicketReduce] = 0;

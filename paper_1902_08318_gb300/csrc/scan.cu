@@ -32,6 +32,8 @@ struct M1 {
     return r;
   }
   __device__ static T load(const Job &J, uint32_t t) { return J.s1_rec[t]; }
+  __device__ static T *agg(const Job &J) { return reinterpret_cast<T *>(J.scan_agg1); }
+  __device__ static T *pre(const Job &J) { return reinterpret_cast<T *>(J.scan_pre1); }
   __device__ static void range(const Job &J, uint32_t &lo, uint32_t &hi) { s1_range(J, lo, hi); }
   // the exclusive prefix of tile t as stored (c1 is never read back)
   __device__ static T stored(const Job &J, uint32_t t) {
@@ -66,6 +68,8 @@ struct M2 {
     return r;
   }
   __device__ static T load(const Job &J, uint32_t t) { return J.s2_rec[t]; }
+  __device__ static T *agg(const Job &J) { return reinterpret_cast<T *>(J.scan_agg); }
+  __device__ static T *pre(const Job &J) { return reinterpret_cast<T *>(J.scan_pre); }
   __device__ static void range(const Job &J, uint32_t &lo, uint32_t &hi) { s2_range(J, lo, hi); }
   // the exclusive prefix of tile t as stored (mn is never read back)
   __device__ static T stored(const Job &J, uint32_t t) {
@@ -127,7 +131,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_up_kernel(const Job *__restri
     T v = t < n ? M::load(J, t) : M::identity();
     T total;
     block_inclusive<M>(v, s_warp, total);
-    if (threadIdx.x == 0) reinterpret_cast<T *>(J.scan_agg)[b] = total;
+    if (threadIdx.x == 0) M::agg(J)[b] = total;
   }
 }
 
@@ -148,7 +152,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_top_kernel(const Job *__restr
   __syncthreads();
   for (uint32_t base = 0; base < nb; base += kScanBlock) {
     const uint32_t b = base + threadIdx.x;
-    const T v = b < nb ? reinterpret_cast<const T *>(J.scan_agg)[b] : M::identity();
+    const T v = b < nb ? M::agg(J)[b] : M::identity();
     T total;
     const T incl = block_inclusive<M>(v, s_warp, total);
     s_incl[threadIdx.x] = incl;
@@ -156,7 +160,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_top_kernel(const Job *__restr
     // exclusive prefix of block b: carry . (inclusive of b-1 within this chunk)
     const T carry = s_carry;
     const T excl = threadIdx.x ? M::combine(carry, s_incl[threadIdx.x - 1]) : carry;
-    if (b < nb) reinterpret_cast<T *>(J.scan_pre)[b] = excl;
+    if (b < nb) M::pre(J)[b] = excl;
     __syncthreads();
     if (threadIdx.x == 0) s_carry = M::combine(carry, total);
     __syncthreads();
@@ -183,7 +187,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
       if (self.head) {
         excl = M::identity();
       } else {
-        const T pre = reinterpret_cast<const T *>(J.scan_pre)[b];
+        const T pre = M::pre(J)[b];
         excl = threadIdx.x ? M::combine(pre, s_incl[threadIdx.x - 1]) : pre;
       }
       M::store(J, t, excl, self);

@@ -78,8 +78,10 @@ struct Job {
   uint64_t *s1_blk;         // per 64-byte block: final mask entered outside / inside a string
   S2Agg *s2_rec;            // per tile
   S2Pre *s2_pre;            // per tile
-  void *scan_agg;           // per scan block (sized for S2Agg)
+  void *scan_agg;           // per scan block (sized for S2Agg): the stage-2 tile scan
   void *scan_pre;           // per scan block
+  void *scan_agg1;          // per scan block: the stage-1 tile scan (its own, so that the two
+  void *scan_pre1;          // scans may run at once on different chunks)
   int32_t *spt;             // sparse table of tile `low` minima: level k at spt + k * spt_stride
   uint32_t spt_stride, spt_levels;
   ulonglong2 *s1_qx;        // per 64-byte block: real quotes, backslash|control bytes
@@ -108,7 +110,9 @@ struct Job {
 // to [11] are the tile tickets of four passes).  A run over
 // resident input sets both to all tiles; a run over a host document that
 // arrives in chunks moves them forward chunk by chunk (chunk_range_kernel).
-constexpr int kCounters = 16;
+// counters[kChunkSlots + c]: the stage-2 bound found after stage 1 of chunk c
+constexpr int kChunkSlots = 16, kMaxChunkSlots = 64;
+constexpr int kCounters = kChunkSlots + kMaxChunkSlots;
 // tile tickets: stage-2 reduce, build and numbers; stage-1 blocks
 constexpr int kTicketReduce = 8, kTicketBuild = 9, kTicketNumbers = 10, kTicketS1 = 11;
 
