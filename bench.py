@@ -3,9 +3,8 @@
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
                     [--workload config2|config1|config0]
 
-A step is one whole parse (setup, first pass, build pass beside the numbers
-kernel, finalize, and the result header copy) of one synthetic document that
-already sits in HBM.  The
+A step is one whole parse (setup, stage 1, stage 2, finalize kernels and the
+result header copy) of one synthetic document that already sits in HBM.  The
 default workload is the 1 GiB single document (records in a root array, ~30%
 non-ASCII string bytes, escape runs across block and tile edges, 1% of records
 nested to depth 1024): larger than L2, so no flush is needed between steps.
@@ -16,11 +15,10 @@ launching stream (max over ranks); a step is one run as sj_parse performs it
 recorded between the stages (direct launches, one stage at a time).  `e2e` is the same metric through sj_parse
 with a pinned host buffer (host-to-device copy inside every step, result
 header read back; the median of three repetitions of up to 10 steps, all
-three listed); the first pass reads the pinned document over the host link
-tile by tile while it parses.  `roofline` reports the algorithmic bytes of
-the whole parse (input, indices, tape, string buffer) over the step time
-against the measured HBM copy bandwidth, with each kernel's share under
-`roofline.kernels`; `cpu_baseline` times the CPU oracle on a bounded
+three listed); a document larger than the parser's largest chunk is copied
+in chunks on a second stream while the kernels parse the chunks that have
+landed.  `roofline` reports the dominant kernel against the
+measured HBM copy bandwidth; `cpu_baseline` times the CPU oracle on a bounded
 sample of the same workload on this host's cores.
 
 Two more objects ride on the same line: `batch` (the 100,000-document batch
@@ -89,10 +87,11 @@ def load_peaks() -> dict:
 
 # The files that define each profiled kernel; host-side code (api.cu,
 # server.cpp, the query and the allocation-free entry) does not change their
-# DRAM traffic, and neither does a change to another pass's kernel.
-_P1 = ("parse1.cu", "s1_common.cuh", "strings.cuh", "sj_internal.cuh")
-_P2 = ("parse2.cu", "strings.cuh", "number.cuh", "pow5_table.h", "sj_internal.cuh")
-KERNEL_SOURCES = {"parse1": _P1, "build": _P2, "numbers": _P2}
+# DRAM traffic, and neither does a change to another stage's kernel.
+_S1 = ("s1.cu", "s1_common.cuh", "sj_internal.cuh")
+_S2 = ("s2.cu", "strings.cuh", "number.cuh", "pow5_table.h", "sj_internal.cuh")
+KERNEL_SOURCES = {"s1_blocks": _S1, "s1_flatten": _S1, "s2_reduce": _S2, "s2_numbers": _S2,
+                  "s2_build": _S2}
 
 
 def source_hash(kernel: str, read=None) -> str:
@@ -173,9 +172,8 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def lexeme_bytes(doc_dev, idx_dev) -> tuple[int, int]:
-    """Input bytes of the string, number and atom lexemes (read by stage 2),
-    and the number of number tokens."""
+def lexeme_bytes(doc_dev, idx_dev) -> int:
+    """Input bytes of the string, number and atom lexemes (read by stage 2)."""
     import torch
     x = doc_dev
     n = idx_dev.numel()
@@ -195,8 +193,7 @@ def lexeme_bytes(doc_dev, idx_dev) -> tuple[int, int]:
             break
         q = q - ws.to(torch.int64)
     del n
-    nums = (first == ord("-")) | ((first >= ord("0")) & (first <= ord("9")))
-    return int((q - p0 + 1).sum().item()), int(nums.sum().item())
+    return int((q - p0 + 1).sum().item())
 
 
 def run_ours(args, rank: int, world: int, dist) -> dict | None:
@@ -221,7 +218,7 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
     if r.error != 0:
         raise SystemExit(f"benchmark document rejected: {r.error_name}")
     S, T, SB = r.n_indices, r.tape_words, r.string_bytes
-    lex, nnum = lexeme_bytes(doc_dev, r.indices()[: S])
+    lex = lexeme_bytes(doc_dev, r.indices()[: S])
     # launch shapes: the autotuner times each main kernel at every allowed
     # shape on this document (outside the timed region)
     tuned = None if args.no_autotune else parser.autotune(doc_dev, stream=stream)
@@ -278,8 +275,8 @@ def run_ours(args, rank: int, world: int, dist) -> dict | None:
         ms_e2e, e2e_steps, e2e_reps = e2e_leg(parser, doc, stream, args, dev, dist)
     if rank != 0:
         return None
-    out = report(args, world, desc, B, S, T, SB, lex, nnum, ms_step, stage_ms, ms_e2e, e2e_steps,
-                 clk, parser.kernels_per_run())
+    out = report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_steps, clk,
+                 parser.kernels_per_run())
     out["ms_per_step_profiled"] = round(ms_profiled, 4)
     if e2e_reps:
         out["e2e"]["ms_per_step_repetitions"] = e2e_reps
@@ -320,35 +317,19 @@ def e2e_leg(parser, doc, stream, args, dev, dist):
     return sorted(reps)[1], e2e_steps, [round(r / e2e_steps, 4) for r in reps]
 
 
-def report(args, world, desc, B, S, T, SB, lex, nnum, ms_step, stage_ms, ms_e2e, e2e_steps, clk,
+def report(args, world, desc, B, S, T, SB, lex, ms_step, stage_ms, ms_e2e, e2e_steps, clk,
            kernels_per_run):
     peaks = load_peaks()
     gbs = world * B / (ms_step * 1e-3) / 1e9
     e2e = world * B / (ms_e2e / e2e_steps * 1e-3) / 1e9
-    # algorithmic bytes of the parse: the input read once and the outputs the
-    # method must produce -- indices, tape, string buffer; each kernel's share
-    # is what it must read or write of that (re-reads are overhead)
     algo_path = B + 4 * S + 8 * T + SB
-    algo = {"setup": 0, "parse1": B + 4 * S, "build": 8 * (T - 2 * nnum) + SB,
-            "numbers": 16 * nnum, "finalize": 0}
+    # algorithmic bytes of each kernel: what it must read or write at minimum
+    algo = {"setup": 0, "s1_blocks": B, "s1_scan": 0, "s1_flatten": 4 * S,
+            "s2_reduce": 4 * S + lex, "s2_scan_frontier": 0, "s2_numbers": 0,
+            "s2_build": 4 * S + lex + 8 * T + SB, "finalize": 0}
     dom = max(stage_ms, key=lambda k: stage_ms[k])
-    kernels = {}
-    traffic_sum, traffic_ok = 0, True
-    for k, ms in stage_ms.items():
-        ent = {"ms": round(ms, 4), "algorithmic_bytes": algo.get(k, 0)}
-        if ms > 0 and algo.get(k, 0):
-            ach = algo[k] / (ms * 1e-3) / 1e9
-            ent["achieved"] = round(ach, 1)
-            ent["frac"] = round(ach / peaks["hbm_gbs"], 4)
-        if k in KERNEL_SOURCES:
-            tr = ncu_traffic(k)
-            ent["traffic"] = tr
-            if tr is None:
-                traffic_ok = False
-            else:
-                traffic_sum += tr
-        kernels[k] = ent
-    achieved = algo_path / (ms_step * 1e-3) / 1e9
+    achieved = algo[dom] / (stage_ms[dom] * 1e-3) / 1e9
+    traffic = ncu_traffic(dom)
     out = {
         "metric": "parse GB/s (input bytes, device-timed)",
         "value": round(gbs, 2),
@@ -363,28 +344,26 @@ def report(args, world, desc, B, S, T, SB, lex, nnum, ms_step, stage_ms, ms_e2e,
         "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: {desc}", "bytes_per_doc": B,
-                   "indices": S, "tape_words": T, "string_bytes": SB, "number_tokens": nnum,
-                   "lexeme_bytes": lex,
+                   "indices": S, "tape_words": T, "string_bytes": SB, "lexeme_bytes": lex,
                    "l2": "inputs larger than L2 (no flush)" if B > 129e6 else "L2 not flushed",
                    "parallelism": f"replicas x{world}"},
-        "roofline": {"bound": "hbm",
-                     "kernel": "whole parse (B + 4S + 8T + SB over the step time)",
-                     "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"], "unit": "GB/s",
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
+                     "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": round(achieved / peaks["hbm_gbs"], 4),
-                     "traffic": traffic_sum if traffic_ok else None,
-                     "traffic_note": "sum of the kernels' DRAM bytes per parse from the committed "
-                                     "ncu capture (profiles/ncu_traffic.json), scaled from a smaller "
-                                     "document of the same recipe by input bytes; null when any "
-                                     "kernel's sources changed since",
-                     "algorithmic_bytes": algo_path,
-                     "input_frac": round(B / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
-                     "dominant": dom, "kernels": kernels,
+                     "traffic": traffic, "algorithmic_bytes": algo[dom],
                      "peak_source": peaks["source"]},
+        "path_roofline": {"algorithmic_bytes": algo_path,
+                          "achieved": round(algo_path / (ms_step * 1e-3) / 1e9, 1),
+                          "frac": round(algo_path / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4),
+                          "input_frac": round(B / (ms_step * 1e-3) / 1e9 / peaks["hbm_gbs"], 4)},
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "e2e": {"value": round(e2e, 3) if e2e == e2e else None, "unit": "GB/s",
                 "h2d_bytes_per_step": B, "d2h_bytes_per_step": 56,
-                "path": "pinned host document read by the first pass over the host link, tile by "
-                        "tile while it parses; the later passes read the device copy it leaves"},
+                "path": ("pinned host document copied in chunks (first 32 MiB, doubling up to "
+                         "512 MiB) on a copy stream; stage 1 of each landed chunk on a second "
+                         "stream, stage 2 on the run's stream as far as the landed chunks allow"
+                         if B > (512 << 20) else
+                         "pinned host document read by stage 1 over the host link")},
         "gpu_launches": kernels_per_run * args.steps,
         "clocks": clk,
     }

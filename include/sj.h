@@ -15,11 +15,8 @@
  *    or sj_doc_result.error, as an sj_error code.
  *  - Input bytes may live in host or device memory (detected with
  *    cudaPointerGetAttributes).  They are read-only and need neither padding
- *    nor alignment.  Device input is read in place.  A single document in
- *    pinned host memory (cudaMallocHost / cudaHostRegister) is read over the
- *    host link by the first pass, tile by tile as it is parsed, which leaves
- *    the device copy the later passes read; other host input is first copied
- *    into a parser-owned device buffer.
+ *    nor alignment.  Host input is first copied into a parser-owned device
+ *    buffer; device input is read in place.
  *  - Outputs live in parser-owned device buffers and stay valid until the next
  *    call on the same parser.  The caller never frees them.
  *  - A parser is not thread-safe; use one parser per host thread.
@@ -111,8 +108,8 @@ typedef struct {
 /* Create a parser for inputs of at most max_bytes bytes in total (summed over
  * a batch) and at most max_docs documents per batch (0 = 1).  max_depth is
  * the nesting limit (0 = 4096; at most 4096); the root container has depth 1.
- * Allocates all device memory up front (about 40 bytes per input byte, plus
- * about 30 MB of per-warp tables; sj_parser_device_bytes tells the total).
+ * Allocates all device memory up front (about 53 bytes per input byte, plus
+ * about 35 MB of per-warp tables; sj_parser_device_bytes tells the total).
  * Returns SJ_SUCCESS and *out, or an error status and *out = NULL. */
 sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint32_t max_docs,
                            uint32_t max_depth);
@@ -218,15 +215,16 @@ sj_status sj_server_replay(sj_server *s, const uint8_t *bytes, const uint64_t *o
 
 /* Per-kernel timing.  With profiling on, runs launch their kernels directly
  * (not through the captured graph) with CUDA events recorded between them on
- * the caller's stream, and the numbers kernel runs after the build pass
- * instead of beside it.  sj_parser_stage_times waits for the last run and
- * writes, in milliseconds, the durations of its 5 stages to ms[0..4]: setup,
- * first pass (stage 1 and the stage-2 scans), build pass, numbers, finalize.
- * n must be at least 5. */
+ * the caller's stream.  sj_parser_stage_times waits for the last run and
+ * writes, in milliseconds, the durations of its 9 stages to ms[0..8]: setup,
+ * stage-1 blocks, stage-1 tile scan, stage-1 flatten, stage-2 reduce, stage-2
+ * tile scan and frontier, stage-2 numbers, stage-2 build, finalize.  n must be
+ * at least 9. */
 sj_status sj_parser_set_profiling(sj_parser *p, int enable);
 sj_status sj_parser_stage_times(sj_parser *p, float *ms, int n);
 
-/* Number of kernel launches in one run of this parser (5). */
+/* Number of kernel launches in one run of this parser (over resident input,
+ * or host input that is not chunked). */
 int sj_parser_kernels_per_run(const sj_parser *p);
 
 /* Capture now the runs (CUDA graphs) of every batch size up to max_docs
@@ -236,10 +234,25 @@ int sj_parser_kernels_per_run(const sj_parser *p);
  * while requests wait. */
 sj_status sj_parser_prepare(sj_parser *p, uint32_t max_docs);
 
-/* Launch shapes.  The three main kernels (first pass, build pass, numbers;
- * arrays of 3 in this order) loop over tiles, so any grid covers any input;
- * the shape is the number of resident blocks per SM, from 1 to the kernel's
- * occupancy limit (max_blocks_per_sm, may be NULL).  A parser starts
+/* Host documents that arrive in chunks.  A single document in pinned host
+ * memory (cudaMallocHost / cudaHostRegister) longer than chunk_bytes is
+ * parsed while it is copied: a second stream copies it chunk by chunk, and
+ * the run's stream runs stage 1 on each chunk once it has landed and stage 2
+ * on every tile whose tokens end in bytes that have landed (Sec. 3 notes that
+ * the two stages can be interleaved over a stream of chunks).  Results are
+ * identical to a parse of the same bytes in device memory.  chunk_bytes is
+ * the largest chunk, rounded up to a multiple of 2048: the first chunk is
+ * 1/16 of it and each next one doubles up to it; at most 64 chunks, the last
+ * taking what remains.  0 turns chunking off (stage 1 then reads the pinned
+ * document over the host link itself); the default is 512 MiB.  Such runs
+ * launch their kernels directly (no graph; about 20 launches per chunk) and
+ * are not profiled: with profiling on, the document is not chunked. */
+sj_status sj_parser_set_host_chunk(sj_parser *p, uint64_t chunk_bytes);
+
+/* Launch shapes.  The four main kernels (stage-1 blocks, stage-1 flatten,
+ * stage-2 reduce, stage-2 build) loop over tiles, so any grid covers any
+ * input; the shape is the number of resident blocks per SM, from 1 to the
+ * kernel's occupancy limit (max_blocks_per_sm, may be NULL).  A parser starts
  * with every kernel at its limit.  sj_parser_set_launch drops the captured
  * graphs (the next run captures again).  The paper has no counterpart: its
  * single-threaded parser has no launch shape. */
@@ -248,9 +261,9 @@ sj_status sj_parser_get_launch(const sj_parser *p, uint32_t *blocks_per_sm,
 sj_status sj_parser_set_launch(sj_parser *p, const uint32_t *blocks_per_sm);
 
 /* Autotuner: parses the sample (bytes, len; host or device) to time each of
- * the three main kernels at every allowed shape, one kernel at a time (reps
+ * the four main kernels at every allowed shape, one kernel at a time (reps
  * timed runs each, after one warm-up), keeps the fastest and writes the
- * choice and its kernel time (ms) to blocks_per_sm[3] / best_ms[3] (either may
+ * choice and its kernel time (ms) to blocks_per_sm[4] / best_ms[4] (either may
  * be NULL).  Leaves profiling as it was.  Synchronous on `stream`. */
 sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len, void *stream,
                              int reps, uint32_t *blocks_per_sm, float *best_ms);
@@ -258,9 +271,8 @@ sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len, v
 /* Stage 1 only (structural indices) of one document, allocating nothing.
  * The paper has no counterpart: this entry exists for callers that cannot call
  * cudaMalloc when they parse (device memory owned by another allocator, or a
- * thread that must not trigger cudaMalloc's implicit synchronisation).  It
- * runs the first pass of sj_parse in its stage-1-only mode, so indices and
- * flags equal those of sj_parse.  The caller passes device buffers: d_bytes (len bytes, read-only), d_indices
+ * thread that must not trigger cudaMalloc's implicit synchronisation).  The
+ * caller passes device buffers: d_bytes (len bytes, read-only), d_indices
  * (room for len u32 positions) and d_result (2 u32: the index count, then
  * flags 1 = invalid UTF-8, 2 = unclosed string, 4 = internal).  The kernel's
  * scratch is one static device array sized for len <= 64 MiB, held by every GPU

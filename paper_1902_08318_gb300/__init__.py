@@ -25,7 +25,8 @@ _ROOT = os.path.dirname(_HERE)
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD, "libsj.so")
-_SOURCES = ["api.cu", "setup.cu", "parse1.cu", "parse2.cu", "noalloc.cu", "server.cpp", "query.cu"]
+_SOURCES = ["api.cu", "s1.cu", "scan.cu", "s2.cu", "stage1.cu", "noalloc.cu", "server.cpp",
+            "query.cu"]
 _HEADERS = ["sj_internal.cuh", "s1_common.cuh", "number.cuh", "strings.cuh", "pow5_table.h"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xptxas", "-O3"]
@@ -137,6 +138,8 @@ def load(path: str | None = None):
     lib.sj_parser_kernels_per_run.restype = ctypes.c_int
     lib.sj_parser_prepare.argtypes = [vp, u32]
     lib.sj_parser_prepare.restype = ctypes.c_int
+    lib.sj_parser_set_host_chunk.argtypes = [vp, u64]
+    lib.sj_parser_set_host_chunk.restype = ctypes.c_int
     lib.sj_stage1_indices_noalloc.argtypes = [vp, u64, vp, vp, vp]
     lib.sj_stage1_indices_noalloc.restype = ctypes.c_int
     lib.sj_error_name.argtypes = [ctypes.c_int]
@@ -198,9 +201,10 @@ EXPORTED = ["sj_parser_create", "sj_parser_destroy", "sj_parse", "sj_parse_async
             "sj_server_submit", "sj_server_poll", "sj_server_release", "sj_server_replay",
             "sj_parser_get_launch", "sj_parser_set_launch", "sj_parser_autotune",
             "sj_query_create", "sj_query_destroy", "sj_query_distinct",
-            "sj_parser_prepare"]
-TUNED_KERNELS = ("parse1", "build", "numbers")
-STAGES = ("setup", "parse1", "build", "numbers", "finalize")
+            "sj_parser_set_host_chunk", "sj_parser_prepare"]
+TUNED_KERNELS = ("s1_blocks", "s1_flatten", "s2_reduce", "s2_build")
+STAGES = ("setup", "s1_blocks", "s1_scan", "s1_flatten", "s2_reduce", "s2_scan_frontier",
+          "s2_numbers", "s2_build", "finalize")
 
 
 class SJError(RuntimeError):
@@ -350,6 +354,11 @@ class Parser:
         """Capture the runs of every batch size up to max_docs now."""
         _check(self._lib.sj_parser_prepare(self._h, int(max_docs)))
 
+    def set_host_chunk(self, chunk_bytes: int):
+        """Chunk size for single documents in pinned host memory, parsed while
+        they are copied (0: never chunk)."""
+        _check(self._lib.sj_parser_set_host_chunk(self._h, int(chunk_bytes)))
+
     @staticmethod
     def view(ptr: int, n: int, typestr: str):
         return _device_tensor(ptr, n, typestr)
@@ -358,9 +367,9 @@ class Parser:
         return int(self._lib.sj_parser_device_bytes(self._h))
 
     def launch(self) -> dict:
-        """Resident blocks per SM of the three tunable kernels, and their limits."""
-        cur = np.zeros(len(TUNED_KERNELS), dtype=np.uint32)
-        lim = np.zeros(len(TUNED_KERNELS), dtype=np.uint32)
+        """Resident blocks per SM of the four main kernels, and their limits."""
+        cur = np.zeros(4, dtype=np.uint32)
+        lim = np.zeros(4, dtype=np.uint32)
         _check(self._lib.sj_parser_get_launch(self._h, cur.ctypes.data, lim.ctypes.data))
         return {k: (int(c), int(m)) for k, c, m in zip(TUNED_KERNELS, cur, lim)}
 
@@ -369,10 +378,10 @@ class Parser:
         _check(self._lib.sj_parser_set_launch(self._h, b.ctypes.data))
 
     def autotune(self, sample, stream=None, reps: int = 2) -> dict:
-        """Pick each tunable kernel's blocks per SM by timing it on `sample`."""
+        """Pick each main kernel's blocks per SM by timing it on `sample`."""
         ptr, n, keep = _as_input(sample)
-        bps = np.zeros(len(TUNED_KERNELS), dtype=np.uint32)
-        ms = np.zeros(len(TUNED_KERNELS), dtype=np.float32)
+        bps = np.zeros(4, dtype=np.uint32)
+        ms = np.zeros(4, dtype=np.float32)
         _check(self._lib.sj_parser_autotune(self._h, ptr, n, _stream_handle(stream), int(reps),
                                             bps.ctypes.data, ms.ctypes.data))
         del keep

@@ -1,16 +1,16 @@
 // api.cu -- the C ABI of include/sj.h: parser objects, launches, results.
 //
 // A run is a fixed sequence of kernels on one stream (see enqueue_run):
-// setup (tiles per document), the first pass (stage 1 and the stage-2 scans,
-// parse1.cu), then the build pass and the numbers kernel side by side on two
-// streams (parse2.cu), and finalize (per-document results), bracketed by a
-// host-to-device copy of the run descriptor and the document offsets and a
-// device-to-host copy of the results.  The sequence is captured once per
-// (parser, bucket of document counts) as a CUDA graph and replayed.
+// setup (tiles per document), stage 1 (blocks, tile scan, flatten), stage 2
+// (reduce, tile scan, frontier, build) and finalize (per-document results),
+// bracketed by a host-to-device copy of the run descriptor and the document
+// offsets and a device-to-host copy of the results.  The sequence is captured
+// once per (parser, bucket of document counts) as a CUDA graph and replayed.
 //
-// A single document in pinned host memory is not copied first: the first
-// pass reads each tile over the host link as it parses it and leaves the
-// device copy that the later passes read.
+// One large document in pinned host memory is parsed as it arrives
+// (enqueue_chunked): a second stream copies it chunk by chunk while the
+// kernels run stage 1 on each chunk that has landed and stage 2 on every tile
+// whose tokens are known to end in landed bytes.
 #include <cuda_runtime.h>
 #include <stdlib.h>
 #include <string.h>
@@ -21,18 +21,24 @@
 
 namespace sj {
 __global__ void setup_kernel(const Job *job);
-__global__ void parse1_kernel(const Job *job);
-__global__ void build_kernel(const Job *job);
+__global__ void stage1_blocks_kernel(const Job *job);
+__global__ void stage1_flatten_kernel(const Job *job);
+__global__ void stage2_reduce_kernel(const Job *job);
+__global__ void stage2_build_kernel(const Job *job);
 __global__ void numbers_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
+__global__ void spt_build_kernel(const Job *job, uint32_t src);
+__global__ void jump_kernel(const Job *job);
+__global__ void frontier_kernel(const Job *job);
+__global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, int mode,
+                                   uint32_t c, int last);
+void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
+void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
 }  // namespace sj
 
 using sj::Job;
 
 static thread_local int g_last_cuda_error = 0;
-
-// the kernels with a tunable launch shape
-enum { kTunedParse1 = 0, kTunedBuild = 1, kTunedNumbers = 2, kTuned = 3 };
 
 struct sj_parser {
   int device = 0;
@@ -40,27 +46,33 @@ struct sj_parser {
   uint32_t max_docs = 0;
   uint32_t max_depth = 0;
   uint64_t max_tiles = 0;
-  uint32_t epoch = 0;  // runs launched (tags the look-back status words)
   // device memory
   uint8_t *d_input = nullptr;
   uint64_t *d_doc_off = nullptr;
   uint32_t *d_tile_first = nullptr;
   uint32_t *d_counters = nullptr;
-  uint64_t *d_st1 = nullptr;
-  uint32_t *d_st2 = nullptr;
-  sj::S2Agg *d_agg2 = nullptr;
-  sj::S2Incl *d_inc2 = nullptr;
-  sj::S2Pre *d_pre2 = nullptr;
-  uint64_t *d_jump = nullptr;
   uint32_t *d_tile_cnt = nullptr;
   uint32_t *d_tile_off = nullptr;
-  uint32_t *d_tile_nstr = nullptr;
-  uint32_t *d_tile_nnum = nullptr;
-  uint32_t *d_surv = nullptr;
+  sj::S1Agg *d_s1_rec = nullptr;
+  sj::S1Pre *d_s1_pre = nullptr;
+  uint64_t *d_s1_blk = nullptr;
+  sj::S2Agg *d_s2_rec = nullptr;
+  sj::S2Pre *d_s2_pre = nullptr;
+  sj::S2Agg *d_scan_agg = nullptr;
+  sj::S2Agg *d_scan_pre = nullptr;
+  sj::S1Agg *d_scan_agg1 = nullptr;
+  sj::S1Agg *d_scan_pre1 = nullptr;
+  int32_t *d_spt = nullptr;
   uint32_t *d_slen = nullptr;
-  uint64_t *d_nlist = nullptr;
+  ulonglong2 *d_s1_qx = nullptr;
+  uint64_t *d_meta = nullptr;
   uint16_t *d_open_g = nullptr;
+  uint8_t *d_unesc = nullptr;
+  uint64_t *d_numv = nullptr;
+  uint32_t *d_nlist = nullptr;
+  uint32_t *d_tile_nnum = nullptr;
   uint64_t *d_front = nullptr;
+  uint32_t *d_surv = nullptr;
   uint32_t *d_idx = nullptr;
   uint64_t *d_tape = nullptr;
   uint8_t *d_strings = nullptr;
@@ -75,21 +87,33 @@ struct sj_parser {
   Job *h_job = nullptr;
   uint64_t *h_doc_off = nullptr;
   sj_doc_result *h_results = nullptr;
-  // launch shapes: grid = SMs x resident blocks per SM
+  // launch shapes
+  int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
+  int num_grid = 0;
   int sms = 0;
-  int occ[kTuned] = {1, 1, 1};    // most resident blocks per SM
-  int grid[kTuned] = {1, 1, 1};
-  int fin_grid = 0;
+  int occ[4] = {1, 1, 1, 1};  // most resident blocks per SM: s1 blocks, flatten, reduce, build
+  uint32_t scan_blocks = 0, scan_grid = 0, spt_levels = 0;
   uint64_t device_bytes = 0;  // cudaMalloc'ed by this parser
   // graph cache: one captured run per document-count bucket (powers of two)
   static constexpr int kBuckets = 33;
   cudaStream_t cap_stream = nullptr;
   cudaGraphExec_t graphs[kBuckets] = {};
   cudaEvent_t done = nullptr;
-  static constexpr int kStages = 5;  // setup, parse1, build, numbers, finalize
+  static constexpr int kStages = 9;
   cudaEvent_t prof[kStages + 1] = {};
-  cudaStream_t aux_stream = nullptr;  // the numbers kernel, beside the build pass
+  // chunked runs over a host document
+  static constexpr uint32_t kMaxChunks = 64;
+  static_assert(kMaxChunks <= (uint32_t)sj::kMaxChunkSlots, "a stage-2 bound slot per chunk");
+  uint64_t host_chunk = 512ull << 20;  // largest chunk; 0 = never chunk
+  cudaStream_t copy_stream = nullptr;
+  cudaStream_t aux_stream = nullptr;  // the numbers kernel, beside the tile scan and frontier
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_start = nullptr;
+  cudaEvent_t ev_chunk[kMaxChunks] = {};
+  cudaStream_t s1_stream = nullptr;  // stage 1 of the chunks, ahead of stage 2
+  cudaEvent_t ev_setup = nullptr;
+  cudaEvent_t ev_s1[kMaxChunks] = {};
+  bool chunked_run = false;
   bool profiling = false;
   bool profiled_run = false;
   bool pending = false;  // an async parse is in flight
@@ -121,17 +145,26 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
   for (cudaGraphExec_t g : p->graphs)
     if (g) cudaGraphExecDestroy(g);
   if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+  if (p->copy_stream) cudaStreamDestroy(p->copy_stream);
   if (p->aux_stream) cudaStreamDestroy(p->aux_stream);
   if (p->ev_fork) cudaEventDestroy(p->ev_fork);
   if (p->ev_join) cudaEventDestroy(p->ev_join);
+  if (p->ev_start) cudaEventDestroy(p->ev_start);
+  if (p->s1_stream) cudaStreamDestroy(p->s1_stream);
+  if (p->ev_setup) cudaEventDestroy(p->ev_setup);
+  for (cudaEvent_t e : p->ev_s1)
+    if (e) cudaEventDestroy(e);
+  for (cudaEvent_t e : p->ev_chunk)
+    if (e) cudaEventDestroy(e);
   if (p->done) cudaEventDestroy(p->done);
   for (cudaEvent_t e : p->prof)
     if (e) cudaEventDestroy(e);
-  void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_st1, p->d_st2,
-                 p->d_agg2, p->d_inc2, p->d_pre2, p->d_jump, p->d_tile_cnt, p->d_tile_off,
-                 p->d_tile_nstr, p->d_tile_nnum, p->d_surv, p->d_slen, p->d_nlist, p->d_open_g,
-                 p->d_front, p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx,
-                 p->d_doc_err, p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job};
+  void *dev[] = {p->d_input, p->d_doc_off, p->d_tile_first, p->d_counters, p->d_tile_cnt,
+                 p->d_tile_off, p->d_s1_rec, p->d_s1_pre, p->d_s1_blk, p->d_s2_rec, p->d_s2_pre,
+                 p->d_scan_agg, p->d_scan_pre, p->d_scan_agg1, p->d_scan_pre1, p->d_spt, p->d_slen, p->d_front, p->d_surv,
+                 p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
+                 p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
+                 p->d_open_g, p->d_unesc, p->d_numv, p->d_nlist, p->d_tile_nnum};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_job) cudaFreeHost(p->h_job);
@@ -147,41 +180,36 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->max_depth = max_depth;
   p->max_tiles = max_bytes / sj::kTileBytes + (uint64_t)max_docs + 1;
   const uint64_t tiles = p->max_tiles;
-  int sms = 0, occ[kTuned] = {0, 0, 0};
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kTunedParse1], sj::parse1_kernel, 128, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kTunedBuild], sj::build_kernel, 128, 0));
-  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[kTunedNumbers], sj::numbers_kernel, 128, 0));
-  p->sms = sms;
-  int max_grid = 1;
-  for (int k = 0; k < kTuned; k++) {
-    p->occ[k] = occ[k] > 0 ? occ[k] : 1;
-    p->grid[k] = sms * p->occ[k];  // default: every SM full (the kernels loop over tiles)
-    if (p->grid[k] > max_grid) max_grid = p->grid[k];
-  }
-  p->fin_grid = sms * 4;
   int r;
   if ((r = dalloc(p, &p->d_input, max_bytes + 64))) return r;
   if ((r = dalloc(p, &p->d_doc_off, (uint64_t)max_docs + 1))) return r;
   if ((r = dalloc(p, &p->d_tile_first, (uint64_t)max_docs + 1))) return r;
   if ((r = dalloc(p, &p->d_counters, sj::kCounters))) return r;
-  if ((r = dalloc(p, &p->d_st1, tiles))) return r;
-  if ((r = dalloc(p, &p->d_st2, tiles))) return r;
-  if ((r = dalloc(p, &p->d_agg2, tiles))) return r;
-  if ((r = dalloc(p, &p->d_inc2, tiles))) return r;
-  if ((r = dalloc(p, &p->d_pre2, tiles))) return r;
-  if ((r = dalloc(p, &p->d_jump, tiles))) return r;
+  p->scan_blocks = (uint32_t)((tiles + sj::kScanBlock - 1) / sj::kScanBlock);
+  p->scan_grid = 0;  // set with the SM count below
+  p->spt_levels = 2;
+  while ((1ull << (p->spt_levels - 1)) <= tiles) p->spt_levels++;
   if ((r = dalloc(p, &p->d_tile_cnt, tiles))) return r;
   if ((r = dalloc(p, &p->d_tile_off, tiles))) return r;
-  if ((r = dalloc(p, &p->d_tile_nstr, tiles))) return r;
-  if ((r = dalloc(p, &p->d_tile_nnum, tiles))) return r;
-  if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_s1_rec, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s1_pre, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s1_blk, tiles * 64))) return r;
+  if ((r = dalloc(p, &p->d_s2_rec, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s2_pre, tiles))) return r;
+  if ((r = dalloc(p, &p->d_scan_agg, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_pre, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_agg1, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_scan_pre1, p->scan_blocks))) return r;
+  if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
   if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
+  if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
+  if ((r = dalloc(p, &p->d_unesc, max_bytes + 64 + 16))) return r;
+  if ((r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_nlist, max_bytes + 16))) return r;
-  // level tables of the two passes' warps (the passes never run at once)
-  const uint64_t open_entries = (uint64_t)max_grid * 4 * sj::kOpenGlobal;
-  if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
+  if ((r = dalloc(p, &p->d_tile_nnum, tiles))) return r;
   if ((r = dalloc(p, &p->d_front, max_bytes + tiles + 16))) return r;
+  if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_idx, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
   if ((r = dalloc(p, &p->d_strings, (5 * max_bytes) / 2 + 8ull * max_docs + 64))) return r;
@@ -193,20 +221,52 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_results, max_docs))) return r;
   if ((r = dalloc(p, &p->d_job, 1))) return r;
   CK(cudaMemset(p->d_counters, 0, sj::kCounters * sizeof(uint32_t)));
-  // epoch 0 is never a run's: zeroed status words read as "not published"
-  CK(cudaMemset(p->d_st1, 0, tiles * sizeof(uint64_t)));
-  CK(cudaMemset(p->d_st2, 0, tiles * sizeof(uint32_t)));
-  CK(cudaMemset(p->d_jump, 0, tiles * sizeof(uint64_t)));
-  CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
   CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
   CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
   CK(cudaMallocHost((void **)&p->h_results, (size_t)max_docs * sizeof(sj_doc_result)));
   CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
+  CK(cudaStreamCreateWithFlags(&p->copy_stream, cudaStreamNonBlocking));
   CK(cudaStreamCreateWithFlags(&p->aux_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->ev_fork, cudaEventDisableTiming));
   CK(cudaEventCreateWithFlags(&p->ev_join, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&p->ev_start, cudaEventDisableTiming));
+  for (cudaEvent_t &e : p->ev_chunk) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  CK(cudaStreamCreateWithFlags(&p->s1_stream, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&p->ev_setup, cudaEventDisableTiming));
+  for (cudaEvent_t &e : p->ev_s1) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+
+  int sms = 0, occ1 = 0, occf = 0, occ2r = 0, occ2b = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, p->device));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ1, sj::stage1_blocks_kernel,
+                                                   32 * sj::kS1Warps, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occf, sj::stage1_flatten_kernel,
+                                                   32 * sj::kS1Warps, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2r, sj::stage2_reduce_kernel,
+                                                   sj::kS2Threads, 0));
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ2b, sj::stage2_build_kernel,
+                                                   sj::kS2Threads, 0));
+  p->sms = sms;
+  p->scan_grid = p->scan_blocks < (uint32_t)(2 * sms) ? p->scan_blocks : (uint32_t)(2 * sms);
+  p->occ[0] = occ1 > 0 ? occ1 : 1;
+  p->occ[1] = occf > 0 ? occf : 1;
+  p->occ[2] = occ2r > 0 ? occ2r : 1;
+  p->occ[3] = occ2b > 0 ? occ2b : 1;
+  // default launch: every SM full (the grids are grid-stride loops over tiles)
+  p->s1_grid = sms * p->occ[0];
+  p->fl_grid = sms * p->occ[1];
+  p->s2r_grid = sms * p->occ[2];
+  p->s2b_grid = sms * p->occ[3];
+  // level tables of the reduce warps (zero between tiles)
+  const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
+  if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
+  CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
+  int occn = 0;
+  CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, sj::numbers_kernel, 128, 0));
+  p->num_grid = sms * (occn > 0 ? occn : 1);
+  p->fin_grid = sms * 4;
+  p->aux_grid = sms * 8;
 
   Job &J = *p->h_job;
   memset(&J, 0, sizeof(J));
@@ -215,21 +275,30 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.max_doc_len = sj::kMaxDocBytes;
   J.tile_first = p->d_tile_first;
   J.counters = p->d_counters;
-  J.st1 = p->d_st1;
-  J.st2 = p->d_st2;
-  J.agg2 = p->d_agg2;
-  J.inc2 = p->d_inc2;
-  J.pre2 = p->d_pre2;
-  J.jump = p->d_jump;
   J.tile_cnt = p->d_tile_cnt;
   J.tile_off = p->d_tile_off;
-  J.tile_nstr = p->d_tile_nstr;
-  J.tile_nnum = p->d_tile_nnum;
-  J.surv = p->d_surv;
+  J.s1_rec = p->d_s1_rec;
+  J.s1_pre = p->d_s1_pre;
+  J.s1_blk = p->d_s1_blk;
+  J.s2_rec = p->d_s2_rec;
+  J.s2_pre = p->d_s2_pre;
+  J.scan_agg = p->d_scan_agg;
+  J.scan_pre = p->d_scan_pre;
+  J.scan_agg1 = p->d_scan_agg1;
+  J.scan_pre1 = p->d_scan_pre1;
+  J.spt = p->d_spt;
+  J.spt_stride = (uint32_t)tiles;
+  J.spt_levels = p->spt_levels;
   J.slen = p->d_slen;
-  J.nlist = p->d_nlist;
+  J.s1_qx = p->d_s1_qx;
+  J.meta = p->d_meta;
   J.open_g = p->d_open_g;
+  J.unesc = p->d_unesc;
+  J.numv = p->d_numv;
+  J.nlist = p->d_nlist;
+  J.tile_nnum = p->d_tile_nnum;
   J.front = p->d_front;
+  J.surv = p->d_surv;
   J.idx = p->d_idx;
   J.tape = p->d_tape;
   J.strings = p->d_strings;
@@ -260,34 +329,58 @@ extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint3
   return SJ_SUCCESS;
 }
 
-// The kernels of one run, in order.  With `ev` (profiled runs), events are
-// recorded before the first kernel and after each of the five stages, and
-// the numbers kernel runs after the build pass instead of beside it.
+// The kernels of one run, in order.  With `ev`, an event is recorded before
+// the first kernel and after each of the stages named in STAGE_NAMES.
+static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+  sj::stage1_blocks_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[2], s);
+  sj::launch_scan1(p->d_job, p->scan_grid, s);
+  if (ev) cudaEventRecord(ev[3], s);
+  sj::stage1_flatten_kernel<<<p->fl_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[4], s);
+}
+
+// Stage 2.  The number conversions need only the reduce pass, and the tile
+// scan and frontier do not touch their data, so (except in profiled runs,
+// which time each stage alone) the numbers kernel runs on a second stream
+// beside the scan and frontier kernels, joined before the build pass.
+static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+  sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[5], s);
+  if (!ev) {
+    cudaEventRecord(p->ev_fork, s);
+    cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
+    sj::numbers_kernel<<<p->num_grid, 128, 0, p->aux_stream>>>(p->d_job);
+    cudaEventRecord(p->ev_join, p->aux_stream);
+  }
+  sj::launch_scan2(p->d_job, p->scan_grid, s);
+  for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
+    sj::spt_build_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job, src);
+  sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
+  sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[6], s);
+  if (ev) sj::numbers_kernel<<<p->num_grid, 128, 0, s>>>(p->d_job);
+  else cudaStreamWaitEvent(s, p->ev_join, 0);
+  if (ev) cudaEventRecord(ev[7], s);
+  sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  if (ev) cudaEventRecord(ev[8], s);
+}
+
 static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[0], s);
   sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[1], s);
-  sj::parse1_kernel<<<p->grid[kTunedParse1], 128, 0, s>>>(p->d_job);
-  if (ev) cudaEventRecord(ev[2], s);
-  if (!ev) {
-    cudaEventRecord(p->ev_fork, s);
-    cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
-    sj::numbers_kernel<<<p->grid[kTunedNumbers], 128, 0, p->aux_stream>>>(p->d_job);
-    cudaEventRecord(p->ev_join, p->aux_stream);
-  }
-  sj::build_kernel<<<p->grid[kTunedBuild], 128, 0, s>>>(p->d_job);
-  if (ev) {
-    cudaEventRecord(ev[3], s);
-    sj::numbers_kernel<<<p->grid[kTunedNumbers], 128, 0, s>>>(p->d_job);
-    cudaEventRecord(ev[4], s);
-  } else {
-    cudaStreamWaitEvent(s, p->ev_join, 0);
-  }
+  enqueue_stage1(p, s, ev);
+  enqueue_stage2(p, s, ev);
   sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
-  if (ev) cudaEventRecord(ev[5], s);
+  if (ev) cudaEventRecord(ev[9], s);
 }
 
-static uint32_t kernels_per_run(const sj_parser *) { return 5; }
+static uint32_t kernels_per_run(const sj_parser *p) {
+  return 2 /* setup, blocks */ + 3 + 1 /* scan1, flatten */ + 1 + 3 /* reduce, scan2 */ +
+         (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 /* numbers */ +
+         1 + 1 /* build, finalize */;
+}
 
 // The launch sequence of one run, captured once per bucket of document
 // counts: the kernels read the count from the run descriptor, and the copies
@@ -354,19 +447,63 @@ static int wait_pending(sj_parser *p) {
   return SJ_SUCCESS;
 }
 
-// The next run's epoch (never 0 in the bits the status words keep).  When it
-// wraps, the status words are cleared so that none of an earlier run can
-// match.
-static int next_epoch(sj_parser *p) {
-  p->epoch++;
-  if ((p->epoch & 0x1FFFFFFFu) == 0) {
-    CK(cudaDeviceSynchronize());
-    CK(cudaMemset(p->d_st1, 0, p->max_tiles * sizeof(uint64_t)));
-    CK(cudaMemset(p->d_st2, 0, p->max_tiles * sizeof(uint32_t)));
-    CK(cudaMemset(p->d_jump, 0, p->max_tiles * sizeof(uint64_t)));
-    p->epoch = 1;
+// One document of `len` bytes in pinned host memory, parsed while it is copied
+// (Sec. 3: stage 1 and stage 2 may run over a stream of chunks).  The copy
+// stream moves the chunks in order, each followed by an event; a stage-1
+// stream waits for chunk c, runs stage 1 on its tiles (the tile scans carry
+// the state of the tiles before) and notes the stage-2 bound the chunk
+// allows; the run's stream waits for that, runs stage 2 on the tiles up to
+// the bound (chunk_range_kernel), and after the last chunk on all that
+// remain.
+static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cudaStream_t s) {
+  // Chunk sizes: a small first chunk (nothing overlaps its copy), then
+  // doubling up to host_chunk; the copies run about twice as fast as the
+  // parse, so each chunk lands before the kernels reach it.  The last of
+  // kMaxChunks chunks takes whatever remains.
+  const uint64_t tile = sj::kTileBytes;
+  const uint64_t cmax = p->host_chunk;
+  uint64_t sz = (cmax / 16 + tile - 1) / tile * tile;
+  uint64_t at[sj_parser::kMaxChunks + 1];
+  uint32_t nc = 0;
+  at[0] = 0;
+  while (at[nc] < len) {
+    const uint64_t o = at[nc];
+    const uint64_t n = nc + 1 == sj_parser::kMaxChunks || len - o < sz ? len - o : sz;
+    at[++nc] = o + n;
+    sz = sz * 2 < cmax ? sz * 2 : cmax;
   }
-  p->h_job->epoch = p->epoch;
+  CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s));
+  CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, 2 * sizeof(uint64_t), cudaMemcpyHostToDevice, s));
+  // the input buffer is free once the work queued before this run is done
+  CK(cudaEventRecord(p->ev_start, s));
+  CK(cudaStreamWaitEvent(p->copy_stream, p->ev_start, 0));
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaMemcpyAsync(p->d_input + at[c], host + at[c], at[c + 1] - at[c], cudaMemcpyHostToDevice,
+                       p->copy_stream));
+    CK(cudaEventRecord(p->ev_chunk[c], p->copy_stream));
+  }
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  // stage 1 of every chunk on its own stream, as the chunks land: it reads
+  // landed bytes and writes the arrays of its own tiles only (its tile scan
+  // has its own scratch), so it runs beside stage 2 of the chunks before
+  CK(cudaEventRecord(p->ev_setup, s));
+  CK(cudaStreamWaitEvent(p->s1_stream, p->ev_setup, 0));
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaStreamWaitEvent(p->s1_stream, p->ev_chunk[c], 0));
+    sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(
+        p->d_job, (uint32_t)(at[c] / tile), (uint32_t)((at[c + 1] + tile - 1) / tile), 0, c, 0);
+    enqueue_stage1(p, p->s1_stream, nullptr);
+    sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(p->d_job, 0, 0, 1, c, 0);
+    CK(cudaEventRecord(p->ev_s1[c], p->s1_stream));
+  }
+  for (uint32_t c = 0; c < nc; c++) {
+    CK(cudaStreamWaitEvent(s, p->ev_s1[c], 0));
+    sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
+    enqueue_stage2(p, s, nullptr);
+  }
+  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
+  CK(cudaGetLastError());
   return SJ_SUCCESS;
 }
 
@@ -376,18 +513,28 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
   int r;
   if ((r = wait_pending(p))) return r;
   const uint8_t *base = bytes, *src = nullptr;
+  bool chunked = false;
   if (!is_device_ptr(bytes)) {
-    // one document in pinned host memory: the first pass reads it over the
-    // host link and writes the device copy; any other host input is copied
+    // one document in pinned host memory: parsed while it is copied when it
+    // spans several chunks, else stage 1 reads it over the host link and
+    // writes the device copy; any other host input is copied first
     src = n_docs == 1 && total ? pinned_device_ptr(bytes) : nullptr;
-    if (!src) CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
+    chunked = src && p->host_chunk && total > p->host_chunk && !p->profiling;
+    if (chunked) src = nullptr;
+    else if (!src) CK(cudaMemcpyAsync(p->d_input, bytes, total, cudaMemcpyHostToDevice, stream));
     base = p->d_input;
   }
   p->h_job->base = base;
   p->h_job->src = src;
+  // the scratch copy of escaped strings keeps the input's alignment modulo 16
+  // (the build pass stages both windows alike)
+  p->h_job->unesc = p->d_unesc + (((uintptr_t)base + p->h_doc_off[0]) & 15u);
   p->h_job->n_docs = n_docs;
-  if ((r = next_epoch(p))) return r;
-  if (p->profiling) {
+  p->chunked_run = chunked;
+  if (chunked) {
+    if ((r = enqueue_chunked(p, bytes, total, stream))) return r;
+    p->profiled_run = false;
+  } else if (p->profiling) {
     // the same sequence as the graph, with events between the kernels
     CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
@@ -536,6 +683,14 @@ extern "C" sj_status sj_parser_prepare(sj_parser *p, uint32_t max_docs) {
   return SJ_SUCCESS;
 }
 
+extern "C" sj_status sj_parser_set_host_chunk(sj_parser *p, uint64_t chunk_bytes) {
+  if (!p) return SJ_INVALID_ARG;
+  int r;
+  if ((r = wait_pending(p))) return r;
+  p->host_chunk = (chunk_bytes + sj::kTileBytes - 1) / sj::kTileBytes * sj::kTileBytes;
+  return SJ_SUCCESS;
+}
+
 extern "C" int sj_parser_kernels_per_run(const sj_parser *p) {
   return p ? (int)kernels_per_run(p) : 0;
 }
@@ -552,8 +707,9 @@ static void drop_graphs(sj_parser *p) {
 extern "C" sj_status sj_parser_get_launch(const sj_parser *p, uint32_t *blocks_per_sm,
                                           uint32_t *max_blocks_per_sm) {
   if (!p || !blocks_per_sm) return SJ_INVALID_ARG;
-  for (int k = 0; k < kTuned; k++) {
-    blocks_per_sm[k] = (uint32_t)(p->grid[k] / p->sms);
+  const int g[4] = {p->s1_grid, p->fl_grid, p->s2r_grid, p->s2b_grid};
+  for (int k = 0; k < 4; k++) {
+    blocks_per_sm[k] = (uint32_t)(g[k] / p->sms);
     if (max_blocks_per_sm) max_blocks_per_sm[k] = (uint32_t)p->occ[k];
   }
   return SJ_SUCCESS;
@@ -561,21 +717,23 @@ extern "C" sj_status sj_parser_get_launch(const sj_parser *p, uint32_t *blocks_p
 
 extern "C" sj_status sj_parser_set_launch(sj_parser *p, const uint32_t *blocks_per_sm) {
   if (!p || !blocks_per_sm) return SJ_INVALID_ARG;
-  for (int k = 0; k < kTuned; k++)
+  for (int k = 0; k < 4; k++)
     if (blocks_per_sm[k] < 1 || (int)blocks_per_sm[k] > p->occ[k]) return SJ_INVALID_ARG;
   int r;
   if ((r = wait_pending(p))) return r;
-  // (the level tables are sized for the largest grids)
-  for (int k = 0; k < kTuned; k++) p->grid[k] = p->sms * (int)blocks_per_sm[k];
+  p->s1_grid = p->sms * (int)blocks_per_sm[0];
+  p->fl_grid = p->sms * (int)blocks_per_sm[1];
+  p->s2r_grid = p->sms * (int)blocks_per_sm[2];  // the reduce level tables fit the largest grid
+  p->s2b_grid = p->sms * (int)blocks_per_sm[3];
   drop_graphs(p);
   return SJ_SUCCESS;
 }
 
-// For each of the three tunable kernels in turn, try every resident-block
-// count per SM its occupancy allows (the others fixed at their current
-// choice), time the kernel with events over `reps` parses of the sample, and
-// keep the fastest.  The stages of a run do not share launch shapes, so the
-// kernels are tuned one at a time.
+// For each of the four main kernels in turn, try every resident-block count
+// per SM its occupancy allows (the others fixed at their current choice),
+// time the kernel with events over `reps` parses of the sample, and keep the
+// fastest.  The stages of a run do not share launch shapes, so the kernels
+// are tuned one at a time.
 extern "C" sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint64_t len,
                                         void *stream, int reps, uint32_t *blocks_per_sm,
                                         float *best_ms) {
@@ -585,15 +743,15 @@ extern "C" sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint
   if ((r = wait_pending(p))) return r;
   const bool was_profiling = p->profiling;
   p->profiling = true;
-  static const int stage_of[kTuned] = {1, 2, 3};  // index into the stage times
-  uint32_t cur[kTuned];
+  static const int stage_of[4] = {1, 3, 4, 7};  // index into the stage times
+  uint32_t cur[4];
   sj_parser_get_launch(p, cur, nullptr);
-  float best[kTuned] = {0, 0, 0};
-  for (int k = 0; k < kTuned; k++) {
+  float best[4] = {0, 0, 0, 0};
+  for (int k = 0; k < 4; k++) {
     uint32_t pick = cur[k];
     float pick_ms = 3.4e38f;
     for (int b = 1; b <= p->occ[k]; b++) {
-      uint32_t trial[kTuned] = {cur[0], cur[1], cur[2]};
+      uint32_t trial[4] = {cur[0], cur[1], cur[2], cur[3]};
       trial[k] = (uint32_t)b;
       if ((r = sj_parser_set_launch(p, trial))) break;
       float sum = 0;
@@ -620,9 +778,9 @@ extern "C" sj_status sj_parser_autotune(sj_parser *p, const uint8_t *bytes, uint
   if (r) return r;
   if (r2) return r2;
   if (blocks_per_sm)
-    for (int k = 0; k < kTuned; k++) blocks_per_sm[k] = cur[k];
+    for (int k = 0; k < 4; k++) blocks_per_sm[k] = cur[k];
   if (best_ms)
-    for (int k = 0; k < kTuned; k++) best_ms[k] = best[k];
+    for (int k = 0; k < 4; k++) best_ms[k] = best[k];
   return SJ_SUCCESS;
 }
 
@@ -637,4 +795,4 @@ extern "C" const char *sj_error_name(int code) {
 
 extern "C" int sj_last_cuda_error(void) { return g_last_cuda_error; }
 
-extern "C" const char *sj_version(void) { return "sj-gb300 0.2 (sm_103a)"; }
+extern "C" const char *sj_version(void) { return "sj-gb300 0.1 (sm_103a)"; }

@@ -10,16 +10,11 @@
 // device array that every GPU loading this library holds until the process
 // exits.
 //
-// The kernel is the first pass of the main parse (parse1.cu) run in its
-// stage-1-only mode, so the indices and flags are those of sj_parse.
-//
 // The scratch is sized for documents of at most kNoAllocMaxBytes (64 MiB).
-// Every call shares it and leaves the last call's contents behind; each call
-// sets up the run descriptor and counters afresh, and tags the look-back
-// status words with a new epoch so that those of earlier calls read as not
-// yet published.  Two calls whose kernels overlap on the GPU (different
-// streams, or different host threads on the same device) race on the scratch
-// and give wrong results: serialise them.
+// Every call shares it and leaves the last call's contents behind; the start
+// of each call clears what must start at zero.  Two calls whose kernels
+// overlap on the GPU (different streams, or different host threads on the same
+// device) race on the scratch and give wrong results: serialise them.
 #include <cuda_runtime.h>
 #include <string.h>
 
@@ -29,14 +24,13 @@
 #include "sj_internal.cuh"
 
 namespace sj {
-__global__ void parse1_kernel(const Job *job);
+__global__ void stage1_kernel(const Job *job);
 }  // namespace sj
 
 namespace {
 
 constexpr uint64_t kNoAllocMaxBytes = 64ull << 20;
 constexpr uint32_t kNoAllocTiles = (uint32_t)(kNoAllocMaxBytes / sj::kTileBytes) + 1;
-constexpr uint32_t kEpochMask = 0x1FFFFFFFu;  // the bits a stage-1 status word keeps
 
 // Layout of the scratch array (byte offsets, each 256-byte aligned).
 constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
@@ -44,18 +38,18 @@ constexpr size_t kOffJob = 0;
 constexpr size_t kOffDocOff = align256(kOffJob + sizeof(sj::Job));
 constexpr size_t kOffTileFirst = align256(kOffDocOff + 2 * sizeof(uint64_t));
 constexpr size_t kOffCounters = align256(kOffTileFirst + 2 * sizeof(uint32_t));
-constexpr size_t kOffDocFlags = align256(kOffCounters + sj::kCounters * sizeof(uint32_t));
+constexpr size_t kOffDocFlags = align256(kOffCounters + 4 * sizeof(uint32_t));
 constexpr size_t kOffDocNidx = align256(kOffDocFlags + sizeof(uint32_t));
-constexpr size_t kOffSt1 = align256(kOffDocNidx + sizeof(uint32_t));
-constexpr size_t kOffTileCnt = align256(kOffSt1 + kNoAllocTiles * sizeof(uint64_t));
+constexpr size_t kOffS1State = align256(kOffDocNidx + sizeof(uint32_t));
+constexpr size_t kOffS1Count = align256(kOffS1State + kNoAllocTiles * sizeof(uint32_t));
+constexpr size_t kOffTileCnt = align256(kOffS1Count + kNoAllocTiles * sizeof(uint64_t));
 constexpr size_t kOffTileOff = align256(kOffTileCnt + kNoAllocTiles * sizeof(uint32_t));
 constexpr size_t kScratchBytes = align256(kOffTileOff + kNoAllocTiles * sizeof(uint32_t));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-// Fills the run descriptor and resets the counters in the scratch; with
-// `clear`, also the status words (after the epoch wrapped).
-__global__ void noalloc_init_kernel(sj::Job job, uint64_t len, uint32_t n_tiles, int clear) {
+// Fills the run descriptor and clears the look-back state of the scratch.
+__global__ void noalloc_init_kernel(sj::Job job, uint64_t len, uint32_t n_tiles) {
   unsigned char *s = g_noalloc_scratch;
   const uint32_t tid = blockIdx.x * blockDim.x + threadIdx.x;
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -68,14 +62,18 @@ __global__ void noalloc_init_kernel(sj::Job job, uint64_t len, uint32_t n_tiles,
     tile_first[0] = 0;
     tile_first[1] = n_tiles;
     uint32_t *counters = reinterpret_cast<uint32_t *>(s + kOffCounters);
-    for (int k = 0; k < sj::kCounters; k++) counters[k] = 0;
-    counters[sj::kCtrTiles] = n_tiles;
+    counters[0] = 0;
+    counters[1] = 0;
+    counters[2] = n_tiles;
+    counters[3] = 0;
     *reinterpret_cast<uint32_t *>(s + kOffDocFlags) = 0;
     *reinterpret_cast<uint32_t *>(s + kOffDocNidx) = 0;
   }
-  if (clear) {
-    uint64_t *st = reinterpret_cast<uint64_t *>(s + kOffSt1);
-    for (uint32_t t = tid; t < kNoAllocTiles; t += stride) st[t] = 0;
+  uint32_t *st = reinterpret_cast<uint32_t *>(s + kOffS1State);
+  uint64_t *cnt = reinterpret_cast<uint64_t *>(s + kOffS1Count);
+  for (uint32_t t = tid; t < n_tiles; t += stride) {
+    st[t] = 0;
+    cnt[t] = 0;
   }
 }
 
@@ -89,17 +87,15 @@ __global__ void noalloc_finish_kernel(uint32_t *result) {
 }
 
 // Per-device set-up: the device address of the scratch array and the launch
-// shape of the kernel.  The array's name is only a host-side stand-in in host
-// code, so its device address is asked for once per device, with that device
-// current.  `epoch` counts the calls on the device.
+// shape of the stage-1 kernel.  The array's name is only a host-side stand-in
+// in host code, so its device address is asked for once per device, with that
+// device current.
 constexpr int kMaxDevices = 64;
 struct DeviceSetup {
   std::once_flag once;
   cudaError_t err = cudaSuccess;
   unsigned char *scratch = nullptr;
   int grid = 0;
-  uint32_t epoch = 0;
-  std::mutex mu;
 };
 DeviceSetup g_setup[kMaxDevices];
 
@@ -109,7 +105,8 @@ void setup_device(DeviceSetup &ds, int dev) {
   if (e != cudaSuccess) { ds.err = e; return; }
   int sms = 0, occ = 0;
   e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sj::parse1_kernel, 128, 0);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sj::stage1_kernel, 32 * sj::kS1Warps, 0);
   if (e != cudaSuccess) { ds.err = e; return; }
   ds.scratch = static_cast<unsigned char *>(ptr);
   ds.grid = sms * (occ > 0 ? occ : 1);
@@ -130,16 +127,6 @@ extern "C" sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t 
   std::call_once(ds.once, setup_device, std::ref(ds), dev);
   if (ds.err != cudaSuccess || !ds.scratch) return SJ_INTERNAL;
 
-  int clear = 0;
-  uint32_t epoch;
-  {
-    std::lock_guard<std::mutex> lock(ds.mu);
-    epoch = ++ds.epoch;
-    if ((epoch & kEpochMask) == 0) {  // wrapped: clear the status words this call
-      ds.epoch = epoch = 1;
-      clear = 1;
-    }
-  }
   unsigned char *s = ds.scratch;
   sj::Job job;
   memset(&job, 0, sizeof(job));
@@ -148,11 +135,10 @@ extern "C" sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t 
   job.n_docs = 1;
   job.max_depth = sj::kMaxDepthLimit;
   job.max_doc_len = kNoAllocMaxBytes;
-  job.epoch = epoch;
-  job.s1_only = 1;
   job.tile_first = reinterpret_cast<uint32_t *>(s + kOffTileFirst);
   job.counters = reinterpret_cast<uint32_t *>(s + kOffCounters);
-  job.st1 = reinterpret_cast<uint64_t *>(s + kOffSt1);
+  job.s1_state = reinterpret_cast<uint32_t *>(s + kOffS1State);
+  job.s1_count = reinterpret_cast<uint64_t *>(s + kOffS1Count);
   job.tile_cnt = reinterpret_cast<uint32_t *>(s + kOffTileCnt);
   job.tile_off = reinterpret_cast<uint32_t *>(s + kOffTileOff);
   job.idx = d_indices;
@@ -161,23 +147,10 @@ extern "C" sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t 
 
   const uint32_t n_tiles = (uint32_t)((len + sj::kTileBytes - 1) / sj::kTileBytes);
   cudaStream_t st = (cudaStream_t)stream;
-  // each launch's own status (no cudaGetLastError: an error left by earlier
-  // unrelated work is neither blamed on this call nor cleared by it)
-  {
-    void *args[] = {&job, &len, (void *)&n_tiles, &clear};
-    e = cudaLaunchKernel((const void *)noalloc_init_kernel, dim3(64), dim3(256), args, 0, st);
-    if (e != cudaSuccess) return SJ_INTERNAL;
-  }
-  {
-    const sj::Job *jp = reinterpret_cast<const sj::Job *>(s + kOffJob);
-    void *args[] = {&jp};
-    e = cudaLaunchKernel((const void *)sj::parse1_kernel, dim3(ds.grid), dim3(128), args, 0, st);
-    if (e != cudaSuccess) return SJ_INTERNAL;
-  }
-  {
-    void *args[] = {&d_result};
-    e = cudaLaunchKernel((const void *)noalloc_finish_kernel, dim3(1), dim3(1), args, 0, st);
-    if (e != cudaSuccess) return SJ_INTERNAL;
-  }
-  return SJ_SUCCESS;
+  noalloc_init_kernel<<<64, 256, 0, st>>>(job, len, n_tiles);
+  sj::stage1_kernel<<<ds.grid, 32 * sj::kS1Warps, 0, st>>>(
+      reinterpret_cast<const sj::Job *>(s + kOffJob));
+  noalloc_finish_kernel<<<1, 1, 0, st>>>(d_result);
+  e = cudaGetLastError();
+  return e == cudaSuccess ? SJ_SUCCESS : SJ_INTERNAL;
 }

@@ -1,6 +1,6 @@
-// s1_common.cuh -- building blocks of stage 1 (Sec. 3.1): SWAR classification
-// of 64-byte blocks, the odd-backslash and in-string masks, reading a block
-// from the staged window, and the UTF-8 check.
+// s1_common.cuh -- building blocks of stage 1 (Sec. 3.1) shared by its kernels:
+// SWAR classification of 64-byte blocks, the odd-backslash and in-string masks,
+// block loading, and the UTF-8 check.
 #pragma once
 #include "sj_internal.cuh"
 
@@ -116,9 +116,9 @@ __device__ __forceinline__ uint64_t prefix_xor(uint64_t x) {
 }
 
 // ---------------------------------------------------------------------------
-// A lane's 64-byte block from the staged window (shared memory): 16 words,
-// realigned with funnel shifts when the document is not 4-byte aligned;
-// bytes past the document's end read as spaces.
+// Loading a block of a document (bytes beyond the document become spaces).
+// Every loaded 16-byte chunk is 16-byte aligned and holds at least one byte of
+// the document, so a load never crosses into a page the document does not use.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ uint32_t mask_tail(uint32_t v, int64_t valid) {
   // keep the first `valid` bytes (0..4) of v, the rest become ' '
@@ -128,106 +128,101 @@ __device__ __forceinline__ uint32_t mask_tail(uint32_t v, int64_t valid) {
   return (v & keep) | (0x20202020u & ~keep);
 }
 
-__device__ __forceinline__ void read_block(const uint8_t *s, uint64_t blk, uint64_t len,
-                                           uint32_t (&w)[16]) {
-  if (blk >= len) {
+template <int WS>  // word shift: (address & 15) / 4
+__device__ __forceinline__ void realign(const uint32_t (&c)[20], int bs8, uint32_t (&w)[16]) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) w[j] = 0x20202020u;
+  for (int j = 0; j < 16; j++) {
+    uint32_t lo = c[j + WS], hi = c[j + WS + 1];
+    w[j] = bs8 ? __funnelshift_r(lo, hi, bs8) : lo;
+  }
+}
+
+__device__ __forceinline__ void load_block(const uint8_t *doc, uint64_t len, uint64_t start,
+                                           uint32_t (&w)[16]) {
+  const uint8_t *a = doc + start;
+  uintptr_t ua = (uintptr_t)a;
+  if ((ua & 15) == 0 && start + 64 <= len) {
+    const uint4 *p = reinterpret_cast<const uint4 *>(a);
+#pragma unroll
+    for (int k = 0; k < 4; k++) {
+      uint4 v = __ldg(p + k);
+      w[4 * k + 0] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
+    }
     return;
   }
-  const uintptr_t ua = (uintptr_t)s;
-  const uint32_t *wp = reinterpret_cast<const uint32_t *>(ua & ~(uintptr_t)3);
-  const uint32_t sh = (uint32_t)(ua & 3u) * 8;
-  if (sh == 0) {
-    if ((ua & 15u) == 0) {
-      const uint4 *p = reinterpret_cast<const uint4 *>(ua);
+  // General path: aligned 16-byte chunks covering [a, a+64), realigned.
+  const uintptr_t doc_end = (uintptr_t)doc + len;
+  const uintptr_t a0 = ua & ~(uintptr_t)15;
+  uint32_t c[20];
 #pragma unroll
-      for (int k = 0; k < 4; k++) {
-        const uint4 v = p[k];
-        w[4 * k] = v.x; w[4 * k + 1] = v.y; w[4 * k + 2] = v.z; w[4 * k + 3] = v.w;
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 16; j++) w[j] = wp[j];
-    }
-  } else {
-    uint32_t lo = wp[0];
-#pragma unroll
-    for (int j = 0; j < 16; j++) {
-      const uint32_t hi = wp[j + 1];
-      w[j] = __funnelshift_r(lo, hi, sh);
-      lo = hi;
-    }
+  for (int k = 0; k < 5; k++) {
+    uintptr_t ca = a0 + 16 * k;
+    uint4 v = make_uint4(0x20202020u, 0x20202020u, 0x20202020u, 0x20202020u);
+    if (ca < doc_end && ca + 16 > ua) v = __ldg(reinterpret_cast<const uint4 *>(ca));
+    c[4 * k + 0] = v.x; c[4 * k + 1] = v.y; c[4 * k + 2] = v.z; c[4 * k + 3] = v.w;
   }
-  if (blk + 64 > len) {
+  const int sh = (int)(ua & 15);
+  const int bs8 = (sh & 3) * 8;
+  switch (sh >> 2) {
+    case 0: realign<0>(c, bs8, w); break;
+    case 1: realign<1>(c, bs8, w); break;
+    case 2: realign<2>(c, bs8, w); break;
+    default: realign<3>(c, bs8, w); break;
+  }
+  if (start + 64 > len) {
 #pragma unroll
-    for (int j = 0; j < 16; j++) w[j] = mask_tail(w[j], (int64_t)len - (int64_t)(blk + 4 * j));
+    for (int j = 0; j < 16; j++) w[j] = mask_tail(w[j], (int64_t)len - (int64_t)(start + 4 * j));
   }
 }
 
 // ---------------------------------------------------------------------------
-// UTF-8 check of one 64-byte block (Sec. 3.1.5, Table "tab:unicode").
-// The structure of the sequences is checked on per-byte flags (bit 7 of each
-// byte of a word): the continuation bytes (10xxxxxx) must be exactly the
-// positions that the lead bytes before them require -- one after every
-// 11xxxxxx lead, a second after 111xxxxx, a third after 1111xxxx -- including
-// positions required by leads among the 3 bytes before the block (`prev`, top
-// bytes; missing bytes are 0).  A word's required positions are its lead
-// flags moved up by one, two and three bytes, with the flags of the word
-// before shifted in.  The remaining rules of the table concern single values
-// (C0, C1 and F5-FF never occur; after E0, ED, F0 and F4 the next byte has a
-// narrower range) and are checked at each lead byte, read from the block's
-// bytes `wb` (shared memory).  A lead whose sequence runs past the block is
-// checked by the next block through its `prev`, or here when the document
-// ends with the block.
+// UTF-8 (Sec. 3.1.5, Table "tab:unicode"), one byte at a time over the
+// non-ASCII words of a block.  State: continuation bytes still expected and
+// the allowed range of the next one.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool utf8_block_error_masks(const uint32_t (&w)[16], const uint8_t *wb,
-                                                       uint32_t prev, bool doc_ends_here) {
-  // lead flags of the word before: >= 2-, >= 3- and 4-byte leads
-  uint32_t p2 = prev & (prev << 1) & 0x80808080u;
-  uint32_t p3 = p2 & (prev << 2), p4 = p3 & (prev << 3);
-  uint32_t bad = 0;
-  uint32_t lm[2] = {0, 0};
+struct Utf8State {
+  uint32_t need, lo, hi;
+  bool err;
+};
+
+__device__ __forceinline__ void utf8_step(Utf8State &s, uint32_t c) {
+  if (s.need) {
+    if (c < s.lo || c > s.hi) s.err = true;
+    s.need--;
+    s.lo = 0x80;
+    s.hi = 0xBF;
+  } else if (c >= 0x80) {
+    if (c < 0xC2) s.err = true;
+    else if (c < 0xE0) s.need = 1;
+    else if (c < 0xF0) { s.need = 2; s.lo = c == 0xE0 ? 0xA0 : 0x80; s.hi = c == 0xED ? 0x9F : 0xBF; }
+    else if (c < 0xF5) { s.need = 3; s.lo = c == 0xF0 ? 0x90 : 0x80; s.hi = c == 0xF4 ? 0x8F : 0xBF; }
+    else s.err = true;
+  }
+}
+
+// Returns true if the block (with the 3 bytes before it, `prev` holding them
+// in its top 3 bytes, `nprev` of them inside the document) has a UTF-8 error.
+__device__ __forceinline__ bool utf8_block_error(const uint32_t (&w)[16], uint32_t prev, int nprev,
+                                                 bool doc_ends_here) {
+  Utf8State s{0, 0x80, 0xBF, false};
+  // Rebuild the state at byte 0 from the preceding bytes; errors there belong
+  // to the previous block and are ignored (a stray continuation byte resets).
+  for (int k = 3 - nprev; k < 3; k++) {
+    uint32_t c = (prev >> (8 * (k + 1))) & 0xFF;
+    Utf8State t = s;
+    utf8_step(t, c);
+    if (t.err) t = Utf8State{0, 0x80, 0xBF, false};
+    s = t;
+  }
 #pragma unroll
   for (int j = 0; j < 16; j++) {
-    const uint32_t x = w[j], x1 = x << 1;
-    const uint32_t c = x & ~x1 & 0x80808080u;  // continuation bytes
-    const uint32_t t2 = x & x1 & 0x80808080u;  // lead bytes
-    const uint32_t t3 = t2 & (x << 2), t4 = t3 & (x << 3);
-    const uint32_t req = __funnelshift_l(p2, t2, 8) | __funnelshift_l(p3, t3, 16) |
-                         __funnelshift_l(p4, t4, 24);
-    bad |= req ^ c;
-    lm[j >> 3] |= movemask4(t2) << ((j & 7) * 4);
-    p2 = t2;
-    p3 = t3;
-    p4 = t4;
-  }
-  if (bad) return true;
-  // leads in the last bytes whose sequences run past the document's end
-  if (doc_ends_here && ((p2 & 0x80000000u) | (p3 & 0x80800000u) | (p4 & 0x80808000u))) return true;
-  const uint64_t L = ((uint64_t)lm[1] << 32) | lm[0];
-  // value rules
-  const uint32_t pb = prev >> 24;  // byte -1
-  if (pb == 0xE0 || pb == 0xED || pb == 0xF0 || pb == 0xF4) {
-    const uint32_t b0 = w[0] & 0xFFu;
-    if ((pb == 0xE0 && b0 < 0xA0) || (pb == 0xED && b0 > 0x9F) || (pb == 0xF0 && b0 < 0x90) ||
-        (pb == 0xF4 && b0 > 0x8F))
-      return true;
-  }
-  uint64_t lead = L;
-  while (lead) {
-    const int i = __ffsll((long long)lead) - 1;
-    lead &= lead - 1;
-    const uint32_t b = wb[i];
-    if (b < 0xC2 || b > 0xF4) return true;
-    if (i < 63 && (b == 0xE0 || b == 0xED || b == 0xF0 || b == 0xF4)) {
-      const uint32_t nb = wb[i + 1];
-      if ((b == 0xE0 && nb < 0xA0) || (b == 0xED && nb > 0x9F) || (b == 0xF0 && nb < 0x90) ||
-          (b == 0xF4 && nb > 0x8F))
-        return true;
+    if ((w[j] & 0x80808080u) || s.need) {
+#pragma unroll
+      for (int b = 0; b < 4; b++) utf8_step(s, (w[j] >> (8 * b)) & 0xFF);
     }
   }
-  return false;
+  if (doc_ends_here && s.need) s.err = true;
+  return s.err;
 }
 
 }  // namespace sj

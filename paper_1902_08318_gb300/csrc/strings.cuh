@@ -159,12 +159,9 @@ __device__ __forceinline__ uint32_t special_bits(uint32_t x) {
 // most that one byte (end, error or one escape sequence), so lanes walking
 // different strings stay in step instead of splitting between a copy loop and
 // escape handling.
-// With `endp`, the position of the closing quote is stored there (an escape
-// always shortens a string, so the string holds escapes exactly when its
-// normalised length is below its raw length).
 template <bool WRITE>
 __device__ __forceinline__ uint32_t string_walk8(const uint8_t *s, const uint8_t *lim, int &err,
-                                                 uint8_t *out, const uint8_t **endp = nullptr) {
+                                                 uint8_t *out) {
   uint32_t n = 0;
   const uint8_t *p = s;
   err = 0;
@@ -199,10 +196,7 @@ __device__ __forceinline__ uint32_t string_walk8(const uint8_t *s, const uint8_t
     if (k == 8) continue;
     if (p >= lim) { err = SJ_STRING_ERROR; return n; }
     const uint32_t c = (k < 4 ? lo >> (8 * k) : hi >> (8 * (k - 4))) & 0xFFu;
-    if (c == '"') {
-      if (endp) *endp = p;
-      return n;
-    }
+    if (c == '"') return n;
     if (c != '\\') { err = SJ_UNESCAPED_CHARS; return n; }  // a byte below 0x20
     if (p + 1 >= lim) { err = SJ_STRING_ERROR; return n; }
     const uint32_t e = p[1];

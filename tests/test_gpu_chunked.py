@@ -1,9 +1,10 @@
-"""A single document in pinned host memory is not copied first: the first
-pass reads each tile over the host link while it parses it and leaves the
-device copy that the later passes read.  Every result must equal the parse of
-the same bytes in device memory and the oracle's, for documents whose tokens,
-strings, escape runs, white space and nesting straddle tile edges, and for
-host buffers at odd addresses."""
+"""Host documents parsed while they are copied (sj_parser_set_host_chunk): a
+single document in pinned host memory, longer than one chunk, is copied chunk
+by chunk on a second stream; stage 1 runs on each chunk as it lands and
+stage 2 on the tiles whose tokens end in landed bytes.  Every result must
+equal the parse of the same bytes in device memory and the oracle's, for
+chunk sizes down to one tile and for documents whose tokens, strings, escape
+runs, white space and nesting straddle chunk edges."""
 import numpy as np
 import pytest
 
@@ -15,10 +16,12 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
+K = 2048  # one tile
+
 
 def _long_string_doc():
-    # a string of ~150 KB with escapes and non-ASCII bytes: whole tiles
-    # without an index, and escapes across tile edges
+    # a string of ~150 KB with escapes and non-ASCII bytes: whole chunks
+    # without an index, and escapes across chunk edges
     body = (b"ab\\n\\\"c\xc3\xa9\\u00e9" + b"x" * 61 + b"\\\\") * 1500
     return b'[1, "' + body + b'", {"k": "v", "n": -1.5e-3}, "' + body[:40000] + b'"]'
 
@@ -59,36 +62,54 @@ def _pinned(d, shift=0):
     return t[shift:]
 
 
-@pytest.mark.parametrize("shift", [0, 3])
-def test_host_input_matches_device_input_and_oracle(parser, shift):
-    for name, d in _docs().items():
+@pytest.mark.parametrize("chunk", [K, 8 * K, 33 * K])
+def test_chunked_host_input_matches_device_input_and_oracle(parser, chunk):
+    docs = _docs()
+    for name, d in docs.items():
+        parser.set_host_chunk(0)
         ref = gpuutil.gpu_result(parser, torch.frombuffer(bytearray(d), dtype=torch.uint8).cuda())
-        got = gpuutil.gpu_result(parser, _pinned(d, shift=shift))
-        gpuutil.compare(got, ref, f"{name} shift {shift}: host vs device")
-        gpuutil.compare(got, oracle.parse(d), f"{name} shift {shift}: host vs oracle")
+        parser.set_host_chunk(chunk)
+        got = gpuutil.gpu_result(parser, _pinned(d, shift=3))
+        gpuutil.compare(got, ref, f"{name} chunk {chunk}: chunked vs device")
+        gpuutil.compare(got, oracle.parse(d), f"{name} chunk {chunk}: chunked vs oracle")
+    parser.set_host_chunk(512 << 20)
 
 
-def test_host_runs_interleave_with_other_runs(parser):
-    # host, resident, host again, and a batch: no state leaks between runs
+def test_chunked_runs_interleave_with_other_runs(parser):
+    # chunked, resident, chunked again, and a batch: no state leaks between runs
     docs = _docs()
     a, b = docs["config2_1MiB"], docs["long_string"]
+    parser.set_host_chunk(4 * K)
     for d in (a, b, a):
-        gpuutil.compare(gpuutil.gpu_result(parser, _pinned(d)), oracle.parse(d), "host")
+        gpuutil.compare(gpuutil.gpu_result(parser, _pinned(d)), oracle.parse(d), "chunked")
         dev = torch.frombuffer(bytearray(d), dtype=torch.uint8).cuda()
         gpuutil.compare(gpuutil.gpu_result(parser, dev), oracle.parse(d), "resident")
     small = [docs["config0"], b"[1, 2]", b"tru"]
     buf, off = gpuutil.batch_arrays(small)
     res, _ = parser.parse_batch(buf, off)
     assert [int(e) for e in res["error"]] == [oracle.parse(s)["error"] for s in small]
+    parser.set_host_chunk(512 << 20)
 
 
-def test_larger_host_document():
-    # 20 MiB: ~10,000 tiles, so look-backs reach across many thread blocks
+def test_many_chunks_are_merged(parser):
+    # one-tile chunks: the 64th chunk takes the rest of the document
+    d = _docs()["config2_1MiB"]
+    parser.set_host_chunk(K)  # 63 chunks of one tile, then 450 tiles
+    gpuutil.compare(gpuutil.gpu_result(parser, _pinned(d)), oracle.parse(d), "merged chunks")
+    parser.set_host_chunk(512 << 20)
+
+
+def test_chunks_spanning_several_scan_blocks():
+    # a tile scan covers 1024 tiles (2 MiB) per block: with a largest chunk of
+    # 6 MiB the later chunks span several scan blocks, each scan starting from
+    # the carry of the chunk before
     import paper_1902_08318_gb300 as sj
     d = gen.config2(2011, size=(20 << 20) + 1234).tobytes()
     p = sj.Parser(max_bytes=len(d) + 64)
     ref = gpuutil.gpu_result(p, torch.frombuffer(bytearray(d), dtype=torch.uint8).cuda())
-    got = gpuutil.gpu_result(p, _pinned(d, shift=5))
-    gpuutil.compare(got, ref, "host vs device")
+    for chunk in (6 << 20, (3 << 20) + 2048):
+        p.set_host_chunk(chunk)
+        got = gpuutil.gpu_result(p, _pinned(d, shift=5))
+        gpuutil.compare(got, ref, f"chunk {chunk}: chunked vs device")
     gpuutil.compare(ref, oracle.parse(d), "device vs oracle")
     p.close()

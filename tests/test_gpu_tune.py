@@ -20,16 +20,16 @@ def test_every_shape_gives_the_same_result():
     lim = {k: m for k, (c, m) in p.launch().items()}
     assert all(m >= 1 for m in lim.values())
     ref = [_outputs(p, d) for d in docs]
-    for shape in ([1] * len(sj.TUNED_KERNELS), [lim[k] for k in sj.TUNED_KERNELS],
+    for shape in ([1, 1, 1, 1], [lim[k] for k in sj.TUNED_KERNELS],
                   [max(1, lim[k] // 2) for k in sj.TUNED_KERNELS]):
         p.set_launch(shape)
         assert [c for c, _ in p.launch().values()] == shape
         for d, r in zip(docs, ref):
             gpuutil.compare(_outputs(p, d), r, f"shape {shape}")
     with pytest.raises(sj.SJError):
-        p.set_launch([0, 1, 1])
+        p.set_launch([0, 1, 1, 1])
     with pytest.raises(sj.SJError):
-        p.set_launch([lim["parse1"] + 1, 1, 1])
+        p.set_launch([lim["s1_blocks"] + 1, 1, 1, 1])
 
 
 def test_autotune_picks_valid_shapes_and_keeps_results():
