@@ -8,8 +8,10 @@ with gcc and marshals arguments through ctypes.
 
 Parity status per function (pins live in tests/test_oracle_*.py):
   utf8_valid   pinned: Table "tab:unicode" vs Python's strict utf-8 codec,
-               exhaustive over 1-2 byte sequences, class representatives for
-               3-4 byte sequences.
+               exhaustive over 1-, 2- and 3-byte sequences; 4-byte sequences
+               with every 4-byte lead, every second and third byte and the
+               fourth byte's boundaries, and every lead with class
+               representatives for the last two bytes.
   classify     pinned: the nibble tables printed in Sec. 3.1.2, all 256 bytes.
   stage1       pinned: the 64-byte worked example of Figs. 2-4 (every printed
                mask row) and brute-force equivalence with a literal transcription

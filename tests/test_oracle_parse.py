@@ -220,8 +220,17 @@ def _check_invariants(doc: np.ndarray):
     d = np.cumsum(np.where(np.isin(first, np.frombuffer(b"{[", dtype=np.uint8)), 1,
                            np.where(np.isin(first, np.frombuffer(b"}]", dtype=np.uint8)), -1, 0)))
     assert d.min() >= 0 and d[-1] == 0
-    # no index strictly inside a string: every index byte is outside the
-    # strings found by the descent (an index on '"' starts one)
+    # no index strictly inside a string: each string token's closing quote
+    # (found by a plain scan that skips the byte after every backslash) lies
+    # before the next index, so no index falls between its quotes
+    raw = np.frombuffer(b, dtype=np.uint8)
+    str_at = np.nonzero(first == ord('"'))[0]
+    for k in str_at:
+        p = int(idx[k]) + 1
+        while raw[p] != ord('"'):
+            p += 2 if raw[p] == ord("\\") else 1
+        nxt = int(idx[k + 1]) if k + 1 < len(idx) else len(b)
+        assert p < nxt, (int(idx[k]), p, nxt)
     # opener/closer payloads are mutually inverse
     tags = (tape >> np.uint64(56)).astype(np.uint8)
     pay = (tape & np.uint64(M56)).astype(np.int64)

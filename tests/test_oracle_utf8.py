@@ -1,9 +1,18 @@
 """Pins of the oracle's UTF-8 check (Sec. 3.1.5, Table "tab:unicode").
 
 The independent reference is Python's strict utf-8 codec, a library routine
-implementing the same well-formedness table (RFC 3629).  Coverage: every 1- and
-2-byte sequence; every (lead, second) pair with class representatives for the
-3rd and 4th bytes; random mixed strings; the paper's rejected example 0xb1 0x87.
+implementing the same well-formedness table (RFC 3629).  Coverage: every 1-,
+2- and 3-byte sequence (all 16.7 million of the latter); 4-byte sequences with
+every 4-byte lead (F0-F7), every second and third byte and the fourth byte's
+range boundaries, and every lead from C0 with every second byte and class
+representatives for the last two; random mixed strings; the paper's rejected
+example 0xb1 0x87.
+
+Python's decoder is run over many records at once: each record is followed
+by a newline (ASCII, so no sequence spans two records) and the buffer is
+decoded with errors="surrogateescape", which turns every byte it cannot decode
+into one code point U+DC80-U+DCFF (a code point that valid UTF-8 cannot
+encode); a record is valid exactly when none of its code points is one.
 """
 import os
 
@@ -29,6 +38,38 @@ def _python_valid(recs: np.ndarray) -> np.ndarray:
     return out
 
 
+def _python_valid_bulk(recs: np.ndarray) -> np.ndarray:
+    """Python's strict verdict on each record, many records per decode."""
+    n, w = recs.shape
+    out = np.ones(n, dtype=bool)
+    step = 1 << 18
+    for lo in range(0, n, step):
+        part = recs[lo: lo + step]
+        m = part.shape[0]
+        buf = np.empty((m, w + 1), dtype=np.uint8)
+        buf[:, :w] = part
+        buf[:, w] = 0x0A
+        text = buf.tobytes().decode("utf-8", "surrogateescape")
+        cp = np.frombuffer(text.encode("utf-32-le", "surrogatepass"), dtype=np.uint32)
+        esc = (cp >= 0xDC80) & (cp <= 0xDCFF)
+        nbytes = np.where(cp < 0x80, 1, np.where(cp < 0x800, 2, np.where(cp < 0x10000, 3, 4)))
+        nbytes[esc] = 1
+        start = np.cumsum(nbytes) - nbytes
+        bad = np.zeros(m, dtype=bool)
+        bad[start[esc] // (w + 1)] = True
+        out[lo: lo + m] = ~bad
+    return out
+
+
+def test_bulk_reference_agrees_with_per_record_decoding():
+    rng = np.random.Generator(np.random.PCG64(5))
+    for w in (1, 2, 3, 4, 6):
+        recs = rng.integers(0, 256, size=(3000, w), dtype=np.uint8)
+        recs[::3, 0] = rng.integers(0xC2, 0xF5, size=recs[::3].shape[0], dtype=np.uint8)
+        recs[::3, 1:] = rng.integers(0x80, 0xC0, size=recs[::3, 1:].shape, dtype=np.uint8)
+        assert (_python_valid_bulk(recs) == _python_valid(recs)).all()
+
+
 def test_all_one_and_two_byte_sequences():
     one = np.arange(256, dtype=np.uint8).reshape(-1, 1)
     assert (oracle.utf8_valid_many(one) == _python_valid(one)).all()
@@ -36,17 +77,28 @@ def test_all_one_and_two_byte_sequences():
     assert (oracle.utf8_valid_many(two) == _python_valid(two)).all()
 
 
-def test_three_byte_sequences():
-    a, b, c = np.meshgrid(np.arange(0xC0, 256), np.arange(256), REPS, indexing="ij")
-    recs = np.stack([a.ravel(), b.ravel(), c.ravel()], axis=1).astype(np.uint8)
-    assert (oracle.utf8_valid_many(recs) == _python_valid(recs)).all()
+def test_every_three_byte_sequence():
+    for lead in range(256):  # 65,536 records per lead
+        b, c = np.meshgrid(np.arange(256), np.arange(256), indexing="ij")
+        recs = np.stack([np.full(b.size, lead), b.ravel(), c.ravel()], axis=1).astype(np.uint8)
+        got = oracle.utf8_valid_many(recs)
+        exp = _python_valid_bulk(recs)
+        assert (got == exp).all(), (lead, recs[np.nonzero(got != exp)[0][:3]])
 
 
 def test_four_byte_sequences():
-    leads = np.array([0xC2, 0xE0, 0xED, 0xEF, 0xF0, 0xF1, 0xF3, 0xF4, 0xF5, 0x80], dtype=np.uint8)
-    a, b, c, d = np.meshgrid(leads, np.arange(256), REPS, REPS, indexing="ij")
+    # every 4-byte lead, every second and third byte, the fourth byte's boundaries
+    fourth = np.array([0x00, 0x41, 0x7F, 0x80, 0x8F, 0x90, 0x9F, 0xA0, 0xBF, 0xC0, 0xF4, 0xFF],
+                      dtype=np.uint8)
+    for lead in range(0xF0, 0xF8):
+        b, c, d = np.meshgrid(np.arange(256), np.arange(256), fourth, indexing="ij")
+        recs = np.stack([np.full(b.size, lead), b.ravel(), c.ravel(), d.ravel()],
+                        axis=1).astype(np.uint8)
+        assert (oracle.utf8_valid_many(recs) == _python_valid_bulk(recs)).all(), lead
+    # every lead from C0, every second byte, representatives for the last two
+    a, b, c, d = np.meshgrid(np.arange(0xC0, 256), np.arange(256), REPS, REPS, indexing="ij")
     recs = np.stack([a.ravel(), b.ravel(), c.ravel(), d.ravel()], axis=1).astype(np.uint8)
-    assert (oracle.utf8_valid_many(recs) == _python_valid(recs)).all()
+    assert (oracle.utf8_valid_many(recs) == _python_valid_bulk(recs)).all()
 
 
 def test_random_strings():
