@@ -145,12 +145,26 @@ extern "C" sj_status sj_stage1_indices_noalloc(const uint8_t *d_bytes, uint64_t 
   job.doc_flags = reinterpret_cast<uint32_t *>(s + kOffDocFlags);
   job.doc_nidx = reinterpret_cast<uint32_t *>(s + kOffDocNidx);
 
-  const uint32_t n_tiles = (uint32_t)((len + sj::kTileBytes - 1) / sj::kTileBytes);
+  uint32_t n_tiles = (uint32_t)((len + sj::kTileBytes - 1) / sj::kTileBytes);
   cudaStream_t st = (cudaStream_t)stream;
-  noalloc_init_kernel<<<64, 256, 0, st>>>(job, len, n_tiles);
-  sj::stage1_kernel<<<ds.grid, 32 * sj::kS1Warps, 0, st>>>(
-      reinterpret_cast<const sj::Job *>(s + kOffJob));
-  noalloc_finish_kernel<<<1, 1, 0, st>>>(d_result);
-  e = cudaGetLastError();
-  return e == cudaSuccess ? SJ_SUCCESS : SJ_INTERNAL;
+  // Each launch's own status: an error left by earlier, unrelated work is
+  // neither blamed on this call nor cleared by it (no cudaGetLastError).
+  {
+    void *args[] = {&job, &len, &n_tiles};
+    e = cudaLaunchKernel((const void *)noalloc_init_kernel, dim3(64), dim3(256), args, 0, st);
+    if (e != cudaSuccess) return SJ_INTERNAL;
+  }
+  {
+    const sj::Job *jp = reinterpret_cast<const sj::Job *>(s + kOffJob);
+    void *args[] = {&jp};
+    e = cudaLaunchKernel((const void *)sj::stage1_kernel, dim3(ds.grid), dim3(32 * sj::kS1Warps),
+                         args, 0, st);
+    if (e != cudaSuccess) return SJ_INTERNAL;
+  }
+  {
+    void *args[] = {&d_result};
+    e = cudaLaunchKernel((const void *)noalloc_finish_kernel, dim3(1), dim3(1), args, 0, st);
+    if (e != cudaSuccess) return SJ_INTERNAL;
+  }
+  return SJ_SUCCESS;
 }

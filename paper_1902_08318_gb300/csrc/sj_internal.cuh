@@ -17,7 +17,14 @@ constexpr int kMaxTileTokens = kTileBytes;    // at most one index per byte
 constexpr int kOpenGlobal = 2 * kMaxTileTokens + 1;  // relative levels [-2048, 2048] of one tile
 constexpr uint32_t kMaxDepthLimit = 4096;
 constexpr uint64_t kMaxDocBytes = 0xFFFFFF00ull;  // keeps positions and tape indices in u32
-constexpr uint32_t kSpinLimit = 1u << 24;         // bounded waits (polls) in look-back loops
+// Bounded waits: polls of a look-back status word before a wait gives up
+// (the waiting tile's document is then marked INTERNAL).  A test build sets a
+// small limit to check that a wait which nothing ends does end.
+#ifdef SJ_SPIN_LIMIT
+constexpr uint32_t kSpinLimit = SJ_SPIN_LIMIT;
+#else
+constexpr uint32_t kSpinLimit = 1u << 24;
+#endif
 
 // Per-document flags written by the kernels.
 constexpr uint32_t kFlagUtf8 = 1, kFlagUnclosed = 2, kFlagInternal = 4, kFlagCapacity = 8;
