@@ -54,7 +54,7 @@ extern "C" {
  * token's content. */
 typedef enum {
   SJ_SUCCESS = 0,
-  SJ_CAPACITY = 1,         /* document too large (>= 2^32 - 256 bytes, or above max_bytes) */
+  SJ_CAPACITY = 1,         /* document too large (more than 2^32 - 256 bytes, or above max_bytes) */
   SJ_MEMALLOC = 2,
   SJ_TAPE_ERROR = 3,       /* grammar: misplaced token, unbalanced brackets, trailing content */
   SJ_DEPTH_ERROR = 4,      /* nesting deeper than max_depth */

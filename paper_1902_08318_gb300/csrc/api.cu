@@ -89,6 +89,10 @@ struct sj_parser {
   sj_doc_result *h_results = nullptr;
   // launch shapes
   int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
+  // The most blocks a launch can use: the kernels loop over tiles (4 per
+  // block of the main kernels, 8 per block of the frontier) and documents, so
+  // a parser for small inputs launches no blocks that would find no work.
+  int tile_blocks = 1, aux_blocks = 1, doc_blocks = 1;
   int num_grid = 0;
   int sms = 0;
   int occ[4] = {1, 1, 1, 1};  // most resident blocks per SM: s1 blocks, flatten, reduce, build
@@ -267,6 +271,9 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->num_grid = sms * (occn > 0 ? occn : 1);
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
+  p->tile_blocks = (int)((tiles + 3) / 4);
+  p->aux_blocks = (int)((tiles + 7) / 8);
+  p->doc_blocks = (int)((max_docs + 255) / 256);
 
   Job &J = *p->h_job;
   memset(&J, 0, sizeof(J));
@@ -329,14 +336,16 @@ extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint3
   return SJ_SUCCESS;
 }
 
+static inline int cap(int grid, int most) { return grid < most ? grid : most; }
+
 // The kernels of one run, in order.  With `ev`, an event is recorded before
 // the first kernel and after each of the stages named in STAGE_NAMES.
 static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
-  sj::stage1_blocks_kernel<<<p->s1_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  sj::stage1_blocks_kernel<<<cap(p->s1_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[2], s);
   sj::launch_scan1(p->d_job, p->scan_grid, s);
   if (ev) cudaEventRecord(ev[3], s);
-  sj::stage1_flatten_kernel<<<p->fl_grid, 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  sj::stage1_flatten_kernel<<<cap(p->fl_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
 }
 
@@ -345,24 +354,24 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
 // which time each stage alone) the numbers kernel runs on a second stream
 // beside the scan and frontier kernels, joined before the build pass.
 static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
-  sj::stage2_reduce_kernel<<<p->s2r_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::stage2_reduce_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
   if (!ev) {
     cudaEventRecord(p->ev_fork, s);
     cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
-    sj::numbers_kernel<<<p->num_grid, 128, 0, p->aux_stream>>>(p->d_job);
+    sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, p->aux_stream>>>(p->d_job);
     cudaEventRecord(p->ev_join, p->aux_stream);
   }
   sj::launch_scan2(p->d_job, p->scan_grid, s);
   for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
-    sj::spt_build_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job, src);
-  sj::jump_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
-  sj::frontier_kernel<<<p->aux_grid, 256, 0, s>>>(p->d_job);
+    sj::spt_build_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job, src);
+  sj::jump_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
+  sj::frontier_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
-  if (ev) sj::numbers_kernel<<<p->num_grid, 128, 0, s>>>(p->d_job);
+  if (ev) sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
   else cudaStreamWaitEvent(s, p->ev_join, 0);
   if (ev) cudaEventRecord(ev[7], s);
-  sj::stage2_build_kernel<<<p->s2b_grid, sj::kS2Threads, 0, s>>>(p->d_job);
+  sj::stage2_build_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);
 }
 
@@ -372,7 +381,7 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[1], s);
   enqueue_stage1(p, s, ev);
   enqueue_stage2(p, s, ev);
-  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[9], s);
 }
 
@@ -501,7 +510,7 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
     sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
     enqueue_stage2(p, s, nullptr);
   }
-  sj::finalize_kernel<<<p->fin_grid, 256, 0, s>>>(p->d_job);
+  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   return SJ_SUCCESS;
