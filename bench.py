@@ -547,6 +547,7 @@ def serving_leg(args) -> dict:
                      "max": float(lat.max()) * 1e3, "wall": wall, "batches": srv.batches - b0})
     med = sorted(runs, key=lambda r: r["p99"])[1]
     wall, batches = med["wall"], med["batches"]
+    capacity = serving_capacity(srv, buf, off, arrival)
     return {
         "workload": "config4: 200,000 requests, Poisson arrivals at 50,000/s, log-normal sizes "
                     "(median 4 KB, sigma 2, 64 B - 8 MB), 60% records / 25% number-heavy / "
@@ -560,7 +561,38 @@ def serving_leg(args) -> dict:
         "batches": int(batches), "docs_per_batch": round(n / max(1, batches), 2),
         "timing": "host clock; arrival = scheduled time, done = result seen by the polling loop; "
                   "the run with the median p99 of three timed replays",
+        "capacity": capacity,
     }
+
+
+def serving_capacity(srv, buf, off, arrival, p99_limit_ms: float = 2.0) -> dict:
+    """The highest offered rate the server sustains with p99 latency under
+    p99_limit_ms: the first 100,000 requests of the config-4 trace replayed
+    with their arrival times compressed by rising factors (the same documents
+    and Poisson pattern at 1x, 2x, ... the trace's rate).  Each rate is
+    replayed three times and judged by the median p99; the sweep stops at the
+    first rate over the limit."""
+    n = min(arrival.size, 100_000)
+    arr0 = arrival[:n] - arrival[0]
+    rows, best = [], None
+    for mult in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32):
+        arr = arr0 / mult
+        reps = []
+        for _ in range(3):
+            lat, wall = srv.replay(buf, off[: n + 1], arr)
+            reps.append((pct(lat, 99) * 1e3, pct(lat, 50) * 1e3, wall))
+        p99, p50, wall = sorted(reps)[1]
+        rate = n / float(arr[-1])
+        rows.append({"offered_req_per_s": round(rate), "p50_ms": round(p50, 4),
+                     "p99_ms": round(p99, 4), "served_req_per_s": round(n / wall),
+                     "GB_per_s": round(int(off[n]) / wall / 1e9, 3)})
+        if p99 >= p99_limit_ms:
+            break
+        best = rows[-1]
+    return {"p99_limit_ms": p99_limit_ms, "requests": int(n),
+            "highest_rate_req_per_s": best["offered_req_per_s"] if best else None,
+            "GB_per_s_at_highest": best["GB_per_s"] if best else None, "sweep": rows,
+            "timing": "each rate: the median p99 of three replays"}
 
 
 def cost_model(args) -> dict:
@@ -639,7 +671,8 @@ def cost_model(args) -> dict:
                       "pretty_ns_per_tape_word": round(a["ms"] * 1e6 / a["T"], 4),
                       "minified_ns_per_tape_word": round(b["ms"] * 1e6 / b["T"], 4),
                       "bytes_per_tape_word": [round(a["B"] / a["T"], 2), round(b["B"] / b["T"], 2)]}
-    return {"mode": "cost-model", "documents": rows,
+    ablations = ablation_table(args, dev)
+    return {"mode": "cost-model", "documents": rows, "ablations": ablations,
             "fit_ns": {"per_byte": round(coef[0], 5), "per_index": round(coef[1], 4),
                        "per_float": round(coef[2], 4), "fixed": round(coef[3], 1), "r2": round(r2, 4)},
             "fit_ns_with_string_bytes": {"per_byte": round(coef_sb[0], 5),
@@ -650,6 +683,62 @@ def cost_model(args) -> dict:
             "minification": mini,
             "note": "per-stage ns per input byte from CUDA events; one GB300; synthetic documents "
                     f"of about {mb} MiB"}
+
+
+def ablation_table(args, dev) -> dict:
+    """The GPU analogue of Table "tab:optimization": stage-1 kernel times with
+    one optimisation at a time replaced by its plain form (the variant
+    libraries of sj.ABLATIONS), on a config-2 shaped document of --doc-mb MiB
+    (default 64), ASCII-only records of the same size (where the UTF-8 check
+    can skip blocks) and the config-1 document.  Each variant's indices, tape size
+    and string bytes are checked equal to the default library's on the device
+    (their parity with the oracle is a GPU test); times are medians over the
+    profiled parses (CUDA events between the stages)."""
+    import torch
+
+    import gen
+    import paper_1902_08318_gb300 as sj
+    mb = args.doc_mb or 64
+    sj.build_variants()
+    libs = {"default": sj.load()}
+    libs.update({name: sj.load_variant(name) for name in sj.ABLATIONS})
+    docs = {f"config2-shaped {mb} MiB": gen.config2(3, size=mb << 20),
+            f"records, ASCII only, pretty {mb} MiB": gen.records(1, mb << 20, root_array=True),
+            "config1 (2.5 MB)": gen.config1(1000)}
+    reps = max(5, min(args.steps, 20))
+    out = {}
+    for dname, doc in docs.items():
+        d = torch.from_numpy(np.require(doc, requirements=["W"])).to(dev)
+        ref = None
+        rows = {}
+        for vname, lib in libs.items():
+            p = sj.Parser(max_bytes=int(doc.size) + 64, lib=lib)
+            p.set_profiling(True)
+            r = p.parse(d)
+            assert r.error == 0, (vname, dname, r.error_name)
+            got = (r.indices().clone(), r.tape_words, r.string_bytes)
+            if ref is None:
+                ref = got
+            else:
+                assert torch.equal(got[0], ref[0]) and got[1:] == ref[1:], (vname, dname)
+            t = {k: [] for k in ("s1_blocks", "s1_scan", "s1_flatten")}
+            for _ in range(reps):
+                p.parse(d)
+                st = p.stage_times()
+                for k in t:
+                    t[k].append(st[k])
+            p.close()
+            med = {k: float(np.median(v)) for k, v in t.items()}
+            rows[vname] = {"s1_blocks_ms": round(med["s1_blocks"], 4),
+                           "s1_flatten_ms": round(med["s1_flatten"], 4),
+                           "stage1_ms": round(sum(med.values()), 4)}
+        base = rows["default"]["stage1_ms"]
+        for v in rows.values():
+            v["stage1_vs_default"] = round(v["stage1_ms"] / base, 3)
+        out[dname] = rows
+    out["variants"] = {k: v for k, v in sj.ABLATIONS.items()}
+    out["timing"] = f"median of {reps} profiled parses per variant; stage 1 = blocks + scan + flatten"
+    return out
 
 
 def oracle_gbs(sample: bytes, repeats: int = 1) -> tuple[float, float]:

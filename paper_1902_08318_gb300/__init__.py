@@ -115,7 +115,65 @@ def load(path: str | None = None):
     path = path or LIB_PATH
     if not os.path.exists(path):
         raise RuntimeError(f"CUDA library not built: {path} (run __graft_entry__.build())")
-    lib = ctypes.CDLL(path)
+    _lib = _bind(ctypes.CDLL(path))
+    return _lib
+
+
+# Stage-1 variants for the measurements of "Effect of Specific Optimizations"
+# (Table "tab:optimization"): each swaps one optimised step for its plain form
+# (the macros are described in csrc/s1_common.cuh) and gives the same results.
+ABLATIONS = {
+    "prefix_xor_loop": "SJ_ABL_PREFIX_XOR_LOOP",
+    "quote_parity_shfl": "SJ_ABL_QUOTE_PARITY_SHFL",
+    "compare_classify": "SJ_ABL_COMPARE_CLASSIFY",
+    "utf8_always": "SJ_ABL_UTF8_ALWAYS",
+    "naive_flatten": "SJ_ABL_NAIVE_FLATTEN",
+}
+_variants = {}
+
+
+def _variant_path(name: str) -> str:
+    """Build (when stale) the library with stage-1 variant `name`: s1.cu
+    compiled with the variant's macro, linked with the library's other
+    objects into _build/variants/libsj_<name>.so."""
+    macro = ABLATIONS[name]
+    vdir = os.path.join(_BUILD, "variants")
+    os.makedirs(vdir, exist_ok=True)
+    out = os.path.join(vdir, f"libsj_{name}.so")
+    deps = [os.path.join(_CSRC, f) for f in ("s1.cu", "s1_common.cuh", "sj_internal.cuh")] + [LIB_PATH]
+    if os.path.exists(out) and os.path.getmtime(out) >= max(os.path.getmtime(d) for d in deps):
+        return out
+    inc = ["-I", os.path.join(_ROOT, "include"), "-I", _CSRC]
+    obj = os.path.join(vdir, f"s1_{name}.o")
+    subprocess.check_call([_nvcc(), *NVCC_FLAGS, *inc, f"-D{macro}", "-c",
+                           os.path.join(_CSRC, "s1.cu"), "-o", obj])
+    objs = [os.path.join(_BUILD, f + ".o") for f in _SOURCES if f != "s1.cu"]
+    tmp = out + f".tmp{os.getpid()}"
+    subprocess.check_call([_nvcc(), "-gencode", "arch=compute_103a,code=sm_103a", "-shared",
+                           "-o", tmp, obj, *objs, "-lcudart"])
+    os.replace(tmp, out)
+    return out
+
+
+def build_variants(names=None) -> list:
+    """Build the variant libraries (all of ABLATIONS by default) in parallel."""
+    names = list(names or ABLATIONS)
+    build()
+    with ThreadPoolExecutor(len(names)) as ex:
+        return list(ex.map(_variant_path, names))
+
+
+def load_variant(name: str):
+    """The library with one stage-1 variant of ABLATIONS compiled in (built on
+    first use), loaded beside the main library."""
+    if name not in _variants:
+        build()
+        _variants[name] = _bind(ctypes.CDLL(_variant_path(name)))
+    return _variants[name]
+
+
+def _bind(lib):
+    """Declare the argument and result types of the C ABI on a loaded library."""
     vp, u64, u32 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_uint32
     lib.sj_parser_create.argtypes = [ctypes.POINTER(vp), u64, u32, u32]
     lib.sj_parser_create.restype = ctypes.c_int
@@ -188,7 +246,6 @@ def load(path: str | None = None):
     lib.sj_server_release.restype = ctypes.c_int
     lib.sj_server_replay.argtypes = [vp, vp, vp, vp, u32, vp, ctypes.POINTER(ctypes.c_double)]
     lib.sj_server_replay.restype = ctypes.c_int
-    _lib = lib
     return lib
 
 
@@ -281,11 +338,11 @@ class Parser:
     """A parser owning device buffers for inputs up to max_bytes (summed over a
     batch) and max_docs documents per batch."""
 
-    def __init__(self, max_bytes: int, max_docs: int = 1, max_depth: int = 0):
+    def __init__(self, max_bytes: int, max_docs: int = 1, max_depth: int = 0, lib=None):
         import torch
         if not torch.cuda.is_available():
             raise SJError("no CUDA device: the parser has no CPU path")
-        self._lib = load()
+        self._lib = lib if lib is not None else load()
         h = ctypes.c_void_p()
         _check(self._lib.sj_parser_create(ctypes.byref(h), int(max_bytes), int(max_docs),
                                           int(max_depth)))

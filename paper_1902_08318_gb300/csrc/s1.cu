@@ -145,7 +145,11 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
         nprev = blk >= 3 ? 3 : (int)blk;
         for (int k = 0; k < nprev; k++) prev |= (uint32_t)doc[blk - nprev + k] << (8 * (4 - nprev + k));
       }
+#ifdef SJ_ABL_UTF8_ALWAYS
+      const bool need = true;
+#else
       const bool need = m.nonascii != 0 || (prev & (prev << 1) & 0x80808000u);
+#endif
       const bool ends_here = blk < len && blk + 64 >= len;
       if (blk < len && need) {
 #pragma unroll
@@ -176,8 +180,21 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
     if (nb & below) e_lane = (tb >> (31 - __clz(nb & below))) & 1u;
     const uint64_t od = escaped_no_carry(m.bs) ^ (e_lane ? first_non_bs(m.bs) : 0ull);
     const uint64_t Q = m.quote & ~od;
+#ifdef SJ_ABL_QUOTE_PARITY_SHFL
+    const uint32_t qp = __popcll(Q) & 1u;
+    uint32_t qincl = qp;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, qincl, o);
+      if (lane >= o) qincl ^= u;
+    }
+    const uint32_t q_before = qincl ^ qp;
+    const uint32_t q_tile = __shfl_sync(0xFFFFFFFFu, qincl, 31);
+#else
     const unsigned pb = __ballot_sync(0xFFFFFFFFu, __popcll(Q) & 1u);
     const uint32_t q_before = __popc(pb & below) & 1u;  // real quotes in earlier lanes, mod 2
+    const uint32_t q_tile = __popc(pb) & 1u;
+#endif
     const uint64_t RQ = prefix_xor(Q);
 
     // ---- final masks (Figs. "identifyquoteregion", "identifypseudo") for both
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
     J.s1_qx[(uint64_t)t * 32 + lane] = make_ulonglong2(Q, m.bs | ctrl_mask(w));
     if (lane == 0) {
       S1Agg a;
-      a.qpar = __popc(pb) & 1u;
+      a.qpar = q_tile;
       a.c0 = cnt[0];
       a.c1 = cnt[1];
       a.head = tt == 0;
@@ -217,9 +234,11 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
 // memory so that the stores are coalesced.
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job *__restrict__ job) {
   const Job &J = *job;
-  __shared__ uint16_t stage[kS1Warps][kTileBytes];  // tile-relative positions
   const int lane = threadIdx.x & 31;
+#ifndef SJ_ABL_NAIVE_FLATTEN
+  __shared__ uint16_t stage[kS1Warps][kTileBytes];  // tile-relative positions
   uint16_t *out_stage = stage[threadIdx.x >> 5];
+#endif
   uint32_t t_lo, t_hi;
   s1_range(J, t_lo, t_hi);
   const uint32_t warps = gridDim.x * kS1Warps;
@@ -254,16 +273,24 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job
     const uint32_t n = __shfl_sync(0xFFFFFFFFu, incl, 31);
     uint32_t o = incl - c;
     uint64_t s = S;
+    uint32_t *dst = J.idx + idx_base(J, d) + pre.base;
+    const uint32_t t0 = tt * kTileBytes;
+#ifdef SJ_ABL_NAIVE_FLATTEN
+    const uint32_t p0 = t0 + lane * kBlockBytes;
+    while (s) {
+      dst[o++] = p0 + (uint32_t)(__ffsll((long long)s) - 1);
+      s &= s - 1;
+    }
+#else
     const uint32_t rel0 = lane * kBlockBytes;
     while (s) {
       out_stage[o++] = (uint16_t)(rel0 + (uint32_t)(__ffsll((long long)s) - 1));
       s &= s - 1;
     }
     __syncwarp();
-    uint32_t *dst = J.idx + idx_base(J, d) + pre.base;
-    const uint32_t t0 = tt * kTileBytes;
     for (uint32_t k = lane; k < n; k += 32) dst[k] = t0 + out_stage[k];
     __syncwarp();
+#endif
     if (lane == 0) {
       J.tile_cnt[t] = n;
       J.tile_off[t] = pre.base;

@@ -6,6 +6,24 @@
 
 namespace sj {
 
+// Compile-time variants for the measurements of "Effect of Specific
+// Optimizations" (Table "tab:optimization"): each replaces one optimised step
+// of stage 1 by its plain form and computes the same result.  None is set in
+// the library; a variant build defines one of them.
+//   SJ_ABL_PREFIX_XOR_LOOP    in-string mask by the definition of the
+//                             carry-less product with all ones (one XOR of a
+//                             shifted all-ones word per quote) instead of the
+//                             shift-XOR ladder
+//   SJ_ABL_QUOTE_PARITY_SHFL  quote parity of the earlier lanes by a
+//                             five-step shuffle XOR scan instead of a ballot
+//                             and a popcount
+//   SJ_ABL_COMPARE_CLASSIFY   classification by one byte comparison per
+//                             character instead of the nibble tables
+//   SJ_ABL_UTF8_ALWAYS        the UTF-8 check on every block, ASCII or not
+//   SJ_ABL_NAIVE_FLATTEN      each lane stores its block's indices to global
+//                             memory one by one instead of staging them in
+//                             shared memory for coalesced stores
+
 // ---------------------------------------------------------------------------
 // Classification (Sec. 3.1.2): two 16-entry nibble tables whose AND gives the
 // class bits of a byte.  Own tables (the paper's layout, different bits):
@@ -50,6 +68,38 @@ struct BlockMasks {
   uint32_t nonascii;  // OR of all words & 0x80808080
 };
 
+// Bit 7 set in each byte of x equal to c (exact: the low seven bits are
+// added without a carry into the next byte).
+__device__ __forceinline__ uint32_t eq_bytes(uint32_t x, uint32_t c) {
+  const uint32_t t = x ^ (c * 0x01010101u);
+  return ~(((t & 0x7F7F7F7Fu) + 0x7F7F7F7Fu) | t | 0x7F7F7F7Fu);
+}
+
+#ifdef SJ_ABL_COMPARE_CLASSIFY
+// The plain classification the paper compares with: one comparison per
+// structural and white-space character, ORed together.
+__device__ __forceinline__ void classify_block(const uint32_t (&w)[16], BlockMasks &m) {
+  uint32_t bs[2] = {0, 0}, qu[2] = {0, 0}, op[2] = {0, 0}, ws[2] = {0, 0};
+  uint32_t na = 0;
+#pragma unroll
+  for (int j = 0; j < 16; j++) {
+    const uint32_t x = w[j];
+    na |= x;
+    const int h = j >> 3, s = (j & 7) * 4;
+    op[h] |= movemask4(eq_bytes(x, ',') | eq_bytes(x, ':') | eq_bytes(x, '[') | eq_bytes(x, ']') |
+                       eq_bytes(x, '{') | eq_bytes(x, '}')) << s;
+    ws[h] |= movemask4(eq_bytes(x, ' ') | eq_bytes(x, '\t') | eq_bytes(x, '\n') |
+                       eq_bytes(x, '\r')) << s;
+    qu[h] |= movemask4(eq_bytes(x, '"')) << s;
+    bs[h] |= movemask4(eq_bytes(x, '\\')) << s;
+  }
+  m.bs = ((uint64_t)bs[1] << 32) | bs[0];
+  m.quote = ((uint64_t)qu[1] << 32) | qu[0];
+  m.op = ((uint64_t)op[1] << 32) | op[0];
+  m.ws = ((uint64_t)ws[1] << 32) | ws[0];
+  m.nonascii = na & 0x80808080u;
+}
+#else
 __device__ __forceinline__ void classify_block(const uint32_t (&w)[16], BlockMasks &m) {
   uint32_t bs[2] = {0, 0}, qu[2] = {0, 0}, op[2] = {0, 0}, ws[2] = {0, 0};
   uint32_t na = 0;
@@ -69,6 +119,7 @@ __device__ __forceinline__ void classify_block(const uint32_t (&w)[16], BlockMas
   m.ws = ((uint64_t)ws[1] << 32) | ws[0];
   m.nonascii = na & 0x80808080u;
 }
+#endif
 
 // Bytes below 0x20 of a block (exact per byte: with the top three bits kept,
 // a byte is zero exactly when it was a control character).
@@ -105,6 +156,18 @@ __device__ __forceinline__ uint64_t first_non_bs(uint64_t b) {
   return nb & (~nb + 1);  // lowest clear bit of b (0 when b is all ones)
 }
 
+#ifdef SJ_ABL_PREFIX_XOR_LOOP
+// The carry-less product of x with an all-ones word, by its definition: every
+// set bit b of x adds (XOR) the all-ones word shifted left by b.
+__device__ __forceinline__ uint64_t prefix_xor(uint64_t x) {
+  uint64_t r = 0;
+  while (x) {
+    r ^= ~0ull << (__ffsll((long long)x) - 1);
+    x &= x - 1;
+  }
+  return r;
+}
+#else
 __device__ __forceinline__ uint64_t prefix_xor(uint64_t x) {
   x ^= x << 1;
   x ^= x << 2;
@@ -114,6 +177,7 @@ __device__ __forceinline__ uint64_t prefix_xor(uint64_t x) {
   x ^= x << 32;
   return x;
 }
+#endif
 
 // ---------------------------------------------------------------------------
 // Loading a block of a document (bytes beyond the document become spaces).
