@@ -376,31 +376,20 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
       const int32_t D = depth + (int32_t)(vi & 0xFFu) - (lane + 1);
       const int32_t E = D - dl;
       const uint32_t tp = tape + (vi >> 8) - w;
-      // Enclosing container: depth moves by at most one per token, so it is
-      // the last earlier token whose depth-before is smaller (an opener at
-      // E - 1).  Found by a descent over window minima of E; when no token of
-      // this chunk qualifies, the level table holds it.
+      // Enclosing container: the latest earlier opener whose depth after it
+      // equals this token's depth before (depth moves by one per token, so
+      // that container is still open).  Inside the chunk such an opener is
+      // the token just before some token k <= i with E_k = E_i, so one match
+      // on E finds it; when none qualifies, the level table holds it.
       const bool op = valid && is_open(kind);
       const uint16_t my = op ? (uint16_t)(0x8000u | (kind == K_OPEN_OBJ ? 0x4000u : 0u) | tp) : 0;
-      int32_t m1 = valid ? E : 0x7FFFFFFF, m2, m4, m8, m16, u;
-      u = __shfl_up_sync(0xFFFFFFFFu, m1, 1);  m2 = lane >= 1 ? min(m1, u) : m1;
-      u = __shfl_up_sync(0xFFFFFFFFu, m2, 2);  m4 = lane >= 2 ? min(m2, u) : m2;
-      u = __shfl_up_sync(0xFFFFFFFFu, m4, 4);  m8 = lane >= 4 ? min(m4, u) : m4;
-      u = __shfl_up_sync(0xFFFFFFFFu, m8, 8);  m16 = lane >= 8 ? min(m8, u) : m8;
-      // mK at lane i: minimum of E over [i - K + 1, i] (clipped at lane 0)
-      int32_t at = lane - 1;
-      u = __shfl_sync(0xFFFFFFFFu, m16, max(at, 0));
-      if (at >= 0 && u >= E) at -= 16;
-      u = __shfl_sync(0xFFFFFFFFu, m8, max(at, 0));
-      if (at >= 0 && u >= E) at -= 8;
-      u = __shfl_sync(0xFFFFFFFFu, m4, max(at, 0));
-      if (at >= 0 && u >= E) at -= 4;
-      u = __shfl_sync(0xFFFFFFFFu, m2, max(at, 0));
-      if (at >= 0 && u >= E) at -= 2;
-      u = __shfl_sync(0xFFFFFFFFu, m1, max(at, 0));
-      if (at >= 0 && u >= E) at -= 1;
-      uint16_t parent = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, max(at, 0));
-      if (at < 0) parent = (valid && E > -kLevelOff && E <= kLevelOff) ? ot.at(E) : (uint16_t)0;
+      const unsigned after_open = __ballot_sync(0xFFFFFFFFu, op) << 1;
+      const unsigned same_e =
+          __match_any_sync(0xFFFFFFFFu, valid ? (uint32_t)E : (0x80000000u | (uint32_t)lane));
+      const unsigned cand = same_e & after_open & (0xFFFFFFFFu >> (31 - lane));
+      const int hk = 31 - __clz(cand);  // -1 when no token qualifies
+      uint16_t parent = (uint16_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)my, max(hk - 1, 0));
+      if (!cand) parent = (valid && E > -kLevelOff && E <= kLevelOff) ? ot.at(E) : (uint16_t)0;
       // the last opener of each level of this chunk stays open for later tokens
       const unsigned grp = __match_any_sync(0xFFFFFFFFu, op ? D : 0x7FFFFFFF);
       if (op && lane == 31 - __clz(grp)) ot.at(D) = my;
