@@ -20,7 +20,7 @@
 #include "sj_internal.cuh"
 
 namespace sj {
-__global__ void setup_kernel(const Job *job);
+__global__ void setup_kernel(Job *job, const Job *hjob, const uint64_t *hoff, uint32_t n_off);
 __global__ void stage1_blocks_kernel(const Job *job);
 __global__ void stage1_flatten_kernel(const Job *job);
 __global__ void stage2_reduce_kernel(const Job *job);
@@ -34,6 +34,8 @@ __global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, i
                                    uint32_t c, int last);
 void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
 void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
+void launch_scan1_small(const Job *job, cudaStream_t s);
+void launch_scan2_spt_small(const Job *job, cudaStream_t s);
 }  // namespace sj
 
 using sj::Job;
@@ -87,6 +89,12 @@ struct sj_parser {
   Job *h_job = nullptr;
   uint64_t *h_doc_off = nullptr;
   sj_doc_result *h_results = nullptr;
+  // their addresses on the device (small runs read and write them in place)
+  Job *h_job_dev = nullptr;
+  uint64_t *h_doc_off_dev = nullptr;
+  sj_doc_result *h_results_dev = nullptr;
+  // at most kSmallTiles tiles: one-block scans, sparse table built with scan 2
+  bool small = false;
   // launch shapes
   int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
   // The most blocks a launch can use: the kernels loop over tiles (4 per
@@ -228,6 +236,10 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaMallocHost((void **)&p->h_job, sizeof(Job)));
   CK(cudaMallocHost((void **)&p->h_doc_off, ((size_t)max_docs + 1) * sizeof(uint64_t)));
   CK(cudaMallocHost((void **)&p->h_results, (size_t)max_docs * sizeof(sj_doc_result)));
+  CK(cudaHostGetDevicePointer((void **)&p->h_job_dev, p->h_job, 0));
+  CK(cudaHostGetDevicePointer((void **)&p->h_doc_off_dev, p->h_doc_off, 0));
+  CK(cudaHostGetDevicePointer((void **)&p->h_results_dev, p->h_results, 0));
+  p->small = tiles <= sj::kSmallTiles;
   CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
@@ -343,7 +355,8 @@ static inline int cap(int grid, int most) { return grid < most ? grid : most; }
 static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   sj::stage1_blocks_kernel<<<cap(p->s1_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[2], s);
-  sj::launch_scan1(p->d_job, p->scan_grid, s);
+  if (p->small) sj::launch_scan1_small(p->d_job, s);
+  else sj::launch_scan1(p->d_job, p->scan_grid, s);
   if (ev) cudaEventRecord(ev[3], s);
   sj::stage1_flatten_kernel<<<cap(p->fl_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
@@ -353,7 +366,9 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
 // scan and frontier do not touch their data, so (except in profiled runs,
 // which time each stage alone) the numbers kernel runs on a second stream
 // beside the scan and frontier kernels, joined before the build pass.
-static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+// `whole`: the run covers whole documents from tile 0 (not a round of a
+// chunked run), so a small parser may build the sparse table with scan 2.
+static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole) {
   sj::stage2_reduce_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
   if (!ev) {
@@ -362,9 +377,13 @@ static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
     sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, p->aux_stream>>>(p->d_job);
     cudaEventRecord(p->ev_join, p->aux_stream);
   }
-  sj::launch_scan2(p->d_job, p->scan_grid, s);
-  for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
-    sj::spt_build_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job, src);
+  if (p->small && whole) {
+    sj::launch_scan2_spt_small(p->d_job, s);
+  } else {
+    sj::launch_scan2(p->d_job, p->scan_grid, s);
+    for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
+      sj::spt_build_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job, src);
+  }
   sj::jump_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   sj::frontier_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
@@ -375,21 +394,31 @@ static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
   if (ev) cudaEventRecord(ev[8], s);
 }
 
-static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
+// With `zc` the set-up kernel reads the run descriptor and the offsets of
+// n_off documents from pinned host memory (no copy before the run).
+static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool zc, uint32_t n_off) {
   if (ev) cudaEventRecord(ev[0], s);
-  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job, zc ? p->h_job_dev : nullptr,
+                                      zc ? p->h_doc_off_dev : nullptr, zc ? n_off : 0u);
   if (ev) cudaEventRecord(ev[1], s);
   enqueue_stage1(p, s, ev);
-  enqueue_stage2(p, s, ev);
+  enqueue_stage2(p, s, ev, true);
   sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[9], s);
 }
 
 static uint32_t kernels_per_run(const sj_parser *p) {
+  if (p->small)
+    return 2 /* setup, blocks */ + 1 + 1 /* scan1, flatten */ + 1 + 1 /* reduce, scan2 and
+         sparse table */ + 2 /* jump, frontier */ + 1 /* numbers */ + 1 + 1 /* build, finalize */;
   return 2 /* setup, blocks */ + 3 + 1 /* scan1, flatten */ + 1 + 3 /* reduce, scan2 */ +
          (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 /* numbers */ +
          1 + 1 /* build, finalize */;
 }
+
+// Whether a run of n_docs documents (its graph bucket) exchanges its
+// descriptor, offsets and results through pinned host memory.
+static bool zero_copy(const sj_parser *p, uint32_t n_docs);
 
 // The launch sequence of one run, captured once per bucket of document
 // counts: the kernels read the count from the run descriptor, and the copies
@@ -411,13 +440,17 @@ static int ensure_graph(sj_parser *p, uint32_t n_docs, cudaGraphExec_t *out) {
   }
   cudaStream_t s = p->cap_stream;
   cudaGraph_t g = nullptr;
+  const bool zc = nb <= sj::kZeroCopyDocs;
   CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-  cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s);
-  cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)nb + 1) * sizeof(uint64_t),
-                  cudaMemcpyHostToDevice, s);
-  enqueue_run(p, s, nullptr);
-  cudaMemcpyAsync(p->h_results, p->d_results, (size_t)nb * sizeof(sj_doc_result),
-                  cudaMemcpyDeviceToHost, s);
+  if (!zc) {
+    cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, s);
+    cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)nb + 1) * sizeof(uint64_t),
+                    cudaMemcpyHostToDevice, s);
+  }
+  enqueue_run(p, s, nullptr, zc, nb + 1);
+  if (!zc)
+    cudaMemcpyAsync(p->h_results, p->d_results, (size_t)nb * sizeof(sj_doc_result),
+                    cudaMemcpyDeviceToHost, s);
   cudaError_t e = cudaStreamEndCapture(s, &g);
   if (e != cudaSuccess) return cuda_fail(e);
   e = cudaGraphInstantiate(&p->graphs[b], g, 0);
@@ -428,6 +461,11 @@ static int ensure_graph(sj_parser *p, uint32_t n_docs, cudaGraphExec_t *out) {
   }
   *out = p->graphs[b];
   return SJ_SUCCESS;
+}
+
+static bool zero_copy(const sj_parser *p, uint32_t n_docs) {
+  int b;
+  return bucket_of(p, n_docs, &b) <= sj::kZeroCopyDocs;
 }
 
 static bool is_device_ptr(const void *ptr) {
@@ -491,7 +529,7 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
                        p->copy_stream));
     CK(cudaEventRecord(p->ev_chunk[c], p->copy_stream));
   }
-  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job);
+  sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job, nullptr, nullptr, 0u);
   // stage 1 of every chunk on its own stream, as the chunks land: it reads
   // landed bytes and writes the arrays of its own tiles only (its tile scan
   // has its own scratch), so it runs beside stage 2 of the chunks before
@@ -508,7 +546,7 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
   for (uint32_t c = 0; c < nc; c++) {
     CK(cudaStreamWaitEvent(s, p->ev_s1[c], 0));
     sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
-    enqueue_stage2(p, s, nullptr);
+    enqueue_stage2(p, s, nullptr, false);
   }
   sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
@@ -539,6 +577,10 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
   // (the build pass stages both windows alike)
   p->h_job->unesc = p->d_unesc + (((uintptr_t)base + p->h_doc_off[0]) & 15u);
   p->h_job->n_docs = n_docs;
+  // the graph of a small bucket writes the results straight to pinned host
+  // memory; every other run writes them on the device and copies them back
+  const bool zc = !chunked && !p->profiling && zero_copy(p, n_docs);
+  p->h_job->results = zc ? p->h_results_dev : p->d_results;
   p->chunked_run = chunked;
   if (chunked) {
     if ((r = enqueue_chunked(p, bytes, total, stream))) return r;
@@ -548,7 +590,7 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
     CK(cudaMemcpyAsync(p->d_job, p->h_job, sizeof(Job), cudaMemcpyHostToDevice, stream));
     CK(cudaMemcpyAsync(p->d_doc_off, p->h_doc_off, ((size_t)n_docs + 1) * sizeof(uint64_t),
                        cudaMemcpyHostToDevice, stream));
-    enqueue_run(p, stream, p->prof);
+    enqueue_run(p, stream, p->prof, false, 0);
     CK(cudaMemcpyAsync(p->h_results, p->d_results, (size_t)n_docs * sizeof(sj_doc_result),
                        cudaMemcpyDeviceToHost, stream));
     CK(cudaGetLastError());

@@ -862,11 +862,25 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *
 // ---------------------------------------------------------------------------
 // Set-up: tiles per document (one block scan over the documents).
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(1024) setup_kernel(const Job *__restrict__ job) {
+// With hjob, the run descriptor and the n_off document offsets are first
+// copied from pinned host memory (hjob, hoff) into device memory (job and
+// the descriptor's doc_off): a small run then needs no copy operation.
+__global__ void __launch_bounds__(1024) setup_kernel(Job *job, const Job *hjob,
+                                                     const uint64_t *hoff, uint32_t n_off) {
+  static_assert(sizeof(Job) % 4 == 0, "the descriptor is copied in words");
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  if (hjob) {
+    const uint32_t *src = reinterpret_cast<const uint32_t *>(hjob);
+    uint32_t *dst = reinterpret_cast<uint32_t *>(job);
+    for (uint32_t i = tid; i < sizeof(Job) / 4; i += 1024) dst[i] = src[i];
+    __syncthreads();
+    uint64_t *doff = const_cast<uint64_t *>(job->doc_off);
+    for (uint32_t i = tid; i < n_off; i += 1024) doff[i] = hoff[i];
+    __syncthreads();
+  }
   const Job &J = *job;
   __shared__ uint32_t s_warp[32];
   __shared__ uint32_t s_carry;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (tid == 0) s_carry = 0;
   __syncthreads();
   for (uint32_t base = 0; base < J.n_docs; base += 1024) {

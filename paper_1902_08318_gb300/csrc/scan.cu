@@ -196,6 +196,68 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
   }
 }
 
+// The whole scan in one thread block, for parsers of at most kSmallTiles
+// tiles: the block walks the range in steps of kScanBlock tiles and carries
+// the inclusive prefix from one step to the next (the three launches above
+// cost more than they save on a few thousand tiles).  With SPT (stage 2) the
+// same block then builds the sparse table of tile minima in shared memory,
+// one level from the one before (level k: minimum over the 2^k tiles ending
+// at a tile), and writes every level out.
+template <class M, bool SPT>
+__global__ void __launch_bounds__(kScanBlock) scan_single_kernel(const Job *__restrict__ job) {
+  using T = typename M::T;
+  const Job &J = *job;
+  __shared__ T s_warp[32];
+  __shared__ T s_incl[kScanBlock];
+  __shared__ T s_carry;
+  __shared__ int32_t s_low[2][SPT ? kSmallTiles : 1];
+  uint32_t lo, n;
+  M::range(J, lo, n);
+  if (threadIdx.x == 0)
+    s_carry = lo == 0 ? M::identity() : M::combine(M::stored(J, lo - 1), M::load(J, lo - 1));
+  __syncthreads();
+  for (uint32_t base = lo; base < n; base += kScanBlock) {
+    const uint32_t t = base + threadIdx.x;
+    const T self = t < n ? M::load(J, t) : M::identity();
+    T total;
+    const T incl = block_inclusive<M>(self, s_warp, total);
+    s_incl[threadIdx.x] = incl;
+    __syncthreads();
+    const T carry = s_carry;
+    if (t < n) {
+      const T excl = self.head ? M::identity()
+                               : (threadIdx.x ? M::combine(carry, s_incl[threadIdx.x - 1]) : carry);
+      M::store(J, t, excl, self);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) s_carry = M::combine(carry, total);
+    __syncthreads();
+  }
+  if constexpr (SPT) {
+    // whole-document runs only (lo == 0, n <= kSmallTiles)
+    for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) {
+      const int32_t v = J.s2_pre[t].low;
+      s_low[0][t] = v;
+      J.spt[t] = v;
+    }
+    __syncthreads();
+    for (uint32_t k = 1; k < J.spt_levels; k++) {
+      const int32_t *in = s_low[(k - 1) & 1];
+      int32_t *out = s_low[k & 1];
+      const uint32_t step = 1u << (k - 1);
+      for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) {
+        const int32_t v = t >= step ? min(in[t], in[t - step]) : in[t];
+        out[t] = v;
+        J.spt[(uint64_t)k * J.spt_stride + t] = v;
+      }
+      __syncthreads();
+    }
+  }
+}
+
+template __global__ void scan_single_kernel<M1, false>(const Job *);
+template __global__ void scan_single_kernel<M2, true>(const Job *);
+
 template __global__ void scan_up_kernel<M1>(const Job *);
 template __global__ void scan_top_kernel<M1>(const Job *);
 template __global__ void scan_down_kernel<M1>(const Job *);
@@ -212,6 +274,12 @@ void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s) {
   scan_up_kernel<M2><<<blocks, kScanBlock, 0, s>>>(job);
   scan_top_kernel<M2><<<1, kScanBlock, 0, s>>>(job);
   scan_down_kernel<M2><<<blocks, kScanBlock, 0, s>>>(job);
+}
+void launch_scan1_small(const Job *job, cudaStream_t s) {
+  scan_single_kernel<M1, false><<<1, kScanBlock, 0, s>>>(job);
+}
+void launch_scan2_spt_small(const Job *job, cudaStream_t s) {
+  scan_single_kernel<M2, true><<<1, kScanBlock, 0, s>>>(job);
 }
 
 // ---- nearest earlier tile with a lower `low` -----------------------------------

@@ -59,6 +59,13 @@ struct S2Pre {
   uint64_t str_start;
 };
 constexpr int kScanBlock = 1024;  // tiles per thread block in the tile scans
+// Parsers of at most this many tiles (4 MiB of input) scan in one thread
+// block and build the sparse table there; whole-document runs only.
+constexpr uint32_t kSmallTiles = 2048;
+// Runs of at most this many documents take the run descriptor and offsets
+// from pinned host memory in the set-up kernel and write their results
+// there (no copy operations in the run).
+constexpr uint32_t kZeroCopyDocs = 1024;
 
 // Everything a run needs, in device memory (one copy per parser; refreshed
 // by a host-to-device copy before each run so that one captured graph serves
