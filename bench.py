@@ -578,7 +578,7 @@ def serving_capacity(srv, buf, off, arrival, p99_limit_ms: float = 2.0) -> dict:
     n = min(arrival.size, 100_000)
     arr0 = arrival[:n] - arrival[0]
     rows, best = [], None
-    for mult in (1, 2, 3, 4, 6, 8, 12, 16, 24, 32):
+    for mult in (1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 16, 24, 32):
         arr = arr0 / mult
         reps = []
         for _ in range(3):

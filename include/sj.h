@@ -161,7 +161,10 @@ uint64_t sj_parser_device_bytes(const sj_parser *p);
  * several batches are on the GPU at once.  Results stay in the slot's device
  * buffers until every document of the batch has been released.  Slots are
  * created, up to max_slots, while their device memory fits mem_budget
- * (0 = no budget).  Not thread-safe: one host thread drives a server. */
+ * (0 = no budget).  Each slot also holds a small parser (1 MiB, 64
+ * documents, counted in the budget) that runs the batches within those
+ * limits with fewer launches.  Not thread-safe: one host thread drives a
+ * server. */
 typedef struct sj_server sj_server;
 typedef struct {
   uint64_t mem_budget;       /* device bytes all slots may hold together (0 = unlimited) */

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 #include <string.h>
 
+#include <algorithm>
 #include <new>
 
 #include "sj_internal.cuh"
@@ -275,7 +276,10 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->s2r_grid = sms * p->occ[2];
   p->s2b_grid = sms * p->occ[3];
   // level tables of the reduce warps (zero between tiles)
-  const uint64_t open_entries = (uint64_t)p->s2r_grid * (sj::kS2Threads / 32) * sj::kOpenGlobal;
+  // (a reduce launch never has more blocks than its tiles can use: tables for
+  // at most that many blocks)
+  const uint64_t reduce_blocks = std::min<uint64_t>((uint64_t)p->s2r_grid, (tiles + 3) / 4);
+  const uint64_t open_entries = reduce_blocks * (sj::kS2Threads / 32) * sj::kOpenGlobal;
   if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
   CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
   int occn = 0;
