@@ -25,7 +25,9 @@ __global__ void setup_kernel(Job *job, const Job *hjob, const uint64_t *hoff, ui
 __global__ void stage1_blocks_kernel(const Job *job);
 __global__ void stage1_flatten_kernel(const Job *job);
 __global__ void stage2_reduce_kernel(const Job *job);
+__global__ void stage2_reduce_sub_kernel(const Job *job);
 __global__ void stage2_build_kernel(const Job *job);
+__global__ void stage2_build_sub_kernel(const Job *job);
 __global__ void numbers_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
 __global__ void spt_build_kernel(const Job *job, uint32_t src);
@@ -94,8 +96,9 @@ struct sj_parser {
   Job *h_job_dev = nullptr;
   uint64_t *h_doc_off_dev = nullptr;
   sj_doc_result *h_results_dev = nullptr;
-  // at most kSmallTiles tiles: one-block scans, sparse table built with scan 2
-  bool small = false;
+  // at most kSmallTiles stage-2 tiles: one-block scans, sparse table built
+  // with scan 2; with `sub`, stage-2 tiles of a quarter on whole runs
+  bool small = false, sub = false;
   // launch shapes
   int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
   // The most blocks a launch can use: the kernels loop over tiles (4 per
@@ -193,6 +196,12 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->max_depth = max_depth;
   p->max_tiles = max_bytes / sj::kTileBytes + (uint64_t)max_docs + 1;
   const uint64_t tiles = p->max_tiles;
+  // A parser of at most kSubTiles tiles splits each stage-1 tile in four for
+  // stage 2 on whole-document runs (its stage-2 arrays hold four times the
+  // tiles); a parser of at most kSmallTiles stage-2 tiles scans in one block.
+  p->sub = tiles <= sj::kSubTiles;
+  const uint64_t tiles2 = p->sub ? tiles << sj::kSmallShift : tiles;
+  p->small = tiles2 <= sj::kSmallTiles;
   int r;
   if ((r = dalloc(p, &p->d_input, max_bytes + 64))) return r;
   if ((r = dalloc(p, &p->d_doc_off, (uint64_t)max_docs + 1))) return r;
@@ -201,27 +210,27 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->scan_blocks = (uint32_t)((tiles + sj::kScanBlock - 1) / sj::kScanBlock);
   p->scan_grid = 0;  // set with the SM count below
   p->spt_levels = 2;
-  while ((1ull << (p->spt_levels - 1)) <= tiles) p->spt_levels++;
-  if ((r = dalloc(p, &p->d_tile_cnt, tiles))) return r;
-  if ((r = dalloc(p, &p->d_tile_off, tiles))) return r;
+  while ((1ull << (p->spt_levels - 1)) <= tiles2) p->spt_levels++;
+  if ((r = dalloc(p, &p->d_tile_cnt, tiles2))) return r;
+  if ((r = dalloc(p, &p->d_tile_off, tiles2))) return r;
   if ((r = dalloc(p, &p->d_s1_rec, tiles))) return r;
   if ((r = dalloc(p, &p->d_s1_pre, tiles))) return r;
   if ((r = dalloc(p, &p->d_s1_blk, tiles * 64))) return r;
-  if ((r = dalloc(p, &p->d_s2_rec, tiles))) return r;
-  if ((r = dalloc(p, &p->d_s2_pre, tiles))) return r;
+  if ((r = dalloc(p, &p->d_s2_rec, tiles2))) return r;
+  if ((r = dalloc(p, &p->d_s2_pre, tiles2))) return r;
   if ((r = dalloc(p, &p->d_scan_agg, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_scan_pre, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_scan_agg1, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_scan_pre1, p->scan_blocks))) return r;
-  if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles))) return r;
+  if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles2))) return r;
   if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_unesc, max_bytes + 64 + 16))) return r;
   if ((r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_nlist, max_bytes + 16))) return r;
-  if ((r = dalloc(p, &p->d_tile_nnum, tiles))) return r;
-  if ((r = dalloc(p, &p->d_front, max_bytes + tiles + 16))) return r;
+  if ((r = dalloc(p, &p->d_tile_nnum, tiles2))) return r;
+  if ((r = dalloc(p, &p->d_front, max_bytes + tiles2 + 16))) return r;
   if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_idx, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_tape, max_bytes + 3ull * max_docs + 8))) return r;
@@ -240,7 +249,6 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaHostGetDevicePointer((void **)&p->h_job_dev, p->h_job, 0));
   CK(cudaHostGetDevicePointer((void **)&p->h_doc_off_dev, p->h_doc_off, 0));
   CK(cudaHostGetDevicePointer((void **)&p->h_results_dev, p->h_results, 0));
-  p->small = tiles <= sj::kSmallTiles;
   CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
   CK(cudaEventCreateWithFlags(&p->done, cudaEventDisableTiming));
   for (cudaEvent_t &e : p->prof) CK(cudaEventCreate(&e));
@@ -278,7 +286,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   // level tables of the reduce warps (zero between tiles)
   // (a reduce launch never has more blocks than its tiles can use: tables for
   // at most that many blocks)
-  const uint64_t reduce_blocks = std::min<uint64_t>((uint64_t)p->s2r_grid, (tiles + 3) / 4);
+  const uint64_t reduce_blocks = std::min<uint64_t>((uint64_t)p->s2r_grid, (tiles2 + 3) / 4);
   const uint64_t open_entries = reduce_blocks * (sj::kS2Threads / 32) * sj::kOpenGlobal;
   if ((r = dalloc(p, &p->d_open_g, open_entries))) return r;
   CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
@@ -287,8 +295,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   p->num_grid = sms * (occn > 0 ? occn : 1);
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
-  p->tile_blocks = (int)((tiles + 3) / 4);
-  p->aux_blocks = (int)((tiles + 7) / 8);
+  p->tile_blocks = (int)((tiles2 + 3) / 4);
+  p->aux_blocks = (int)((tiles2 + 7) / 8);
   p->doc_blocks = (int)((max_docs + 255) / 256);
 
   Job &J = *p->h_job;
@@ -310,7 +318,7 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.scan_agg1 = p->d_scan_agg1;
   J.scan_pre1 = p->d_scan_pre1;
   J.spt = p->d_spt;
-  J.spt_stride = (uint32_t)tiles;
+  J.spt_stride = (uint32_t)tiles2;
   J.spt_levels = p->spt_levels;
   J.slen = p->d_slen;
   J.s1_qx = p->d_s1_qx;
@@ -373,7 +381,11 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
 // `whole`: the run covers whole documents from tile 0 (not a round of a
 // chunked run), so a small parser may build the sparse table with scan 2.
 static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole) {
-  sj::stage2_reduce_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+  const bool sub = p->sub && whole;  // the run's s2_shift
+  if (sub)
+    sj::stage2_reduce_sub_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+  else
+    sj::stage2_reduce_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[5], s);
   if (!ev) {
     cudaEventRecord(p->ev_fork, s);
@@ -394,7 +406,10 @@ static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool w
   if (ev) sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
   else cudaStreamWaitEvent(s, p->ev_join, 0);
   if (ev) cudaEventRecord(ev[7], s);
-  sj::stage2_build_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+  if (sub)
+    sj::stage2_build_sub_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+  else
+    sj::stage2_build_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[8], s);
 }
 
@@ -581,6 +596,8 @@ static int launch(sj_parser *p, const uint8_t *bytes, uint64_t total, uint32_t n
   // (the build pass stages both windows alike)
   p->h_job->unesc = p->d_unesc + (((uintptr_t)base + p->h_doc_off[0]) & 15u);
   p->h_job->n_docs = n_docs;
+  // stage-2 tiles of a quarter on a small parser's whole-document runs
+  p->h_job->s2_shift = p->sub && !chunked ? sj::kSmallShift : 0u;
   // the graph of a small bucket writes the results straight to pinned host
   // memory; every other run writes them on the device and copies them back
   const bool zc = !chunked && !p->profiling && zero_copy(p, n_docs);

@@ -291,9 +291,18 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job
     for (uint32_t k = lane; k < n; k += 32) dst[k] = t0 + out_stage[k];
     __syncwarp();
 #endif
+    // index count and first index of each stage-2 tile (the tile itself, or
+    // each group of 32 >> s2_shift blocks)
+    {
+      const uint32_t sh = J.s2_shift, grp = 32u >> sh;
+      const uint32_t end_incl = __shfl_sync(0xFFFFFFFFu, incl, lane | (int)(grp - 1));
+      if ((lane & (grp - 1)) == 0) {
+        const uint32_t t2 = (t << sh) + ((uint32_t)lane >> (5 - sh));
+        J.tile_cnt[t2] = end_incl - (incl - c);
+        J.tile_off[t2] = pre.base + incl - c;
+      }
+    }
     if (lane == 0) {
-      J.tile_cnt[t] = n;
-      J.tile_off[t] = pre.base;
       if (tt == ntiles_d - 1) {
         J.doc_nidx[d] = pre.base + n;
         if (pre.q_in ^ J.s1_rec[t].qpar) atomicOr(&J.doc_flags[d], kFlagUnclosed);

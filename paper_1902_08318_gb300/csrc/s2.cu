@@ -99,14 +99,15 @@ struct Staged {
   }
 };
 
-// Copy the tile's bytes and kHalo more (16-byte chunks) into shared memory.
+// Copy n bytes from t0 on (a tile and a halo; at most STAGE) into shared
+// memory in 16-byte chunks; a tile past the document's end stages nothing.
 template <int STAGE = kStageBytes>
 __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc, uint64_t len,
-                                             uint64_t t0, int lane) {
+                                             uint64_t t0, int lane, uint32_t n = STAGE) {
   const uintptr_t g0 = (uintptr_t)(doc + t0);
   const uintptr_t a0 = g0 & ~(uintptr_t)15;
   const uintptr_t dend = (uintptr_t)doc + len;
-  const uintptr_t send = min((uintptr_t)(a0 + STAGE), dend);
+  const uintptr_t send = max(min((uintptr_t)(a0 + min(n, (uint32_t)STAGE)), dend), a0);
   const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
   for (uint32_t c = lane; c < nch; c += 32)
     reinterpret_cast<uint4 *>(bytes)[c] = __ldg(reinterpret_cast<const uint4 *>(a0 + 16 * c));
@@ -126,11 +127,12 @@ __device__ __forceinline__ Staged stage_tile(uint8_t *bytes, const uint8_t *doc,
 // copies (cp.async) into shared memory; wait_staged() completes them.
 template <int STAGE = kStageBytes>
 __device__ __forceinline__ Staged stage_tile_async(uint8_t *bytes, const uint8_t *doc,
-                                                   uint64_t len, uint64_t t0, int lane) {
+                                                   uint64_t len, uint64_t t0, int lane,
+                                                   uint32_t n = STAGE) {
   const uintptr_t g0 = (uintptr_t)(doc + t0);
   const uintptr_t a0 = g0 & ~(uintptr_t)15;
   const uintptr_t dend = (uintptr_t)doc + len;
-  const uintptr_t send = min((uintptr_t)(a0 + STAGE), dend);
+  const uintptr_t send = max(min((uintptr_t)(a0 + min(n, (uint32_t)STAGE)), dend), a0);
   const uint32_t nch = (uint32_t)((send - a0 + 15) / 16);
   for (uint32_t c = lane; c < nch; c += 32) {
     const uint32_t sa = (uint32_t)__cvta_generic_to_shared(bytes + 16 * c);
@@ -257,7 +259,10 @@ __device__ __forceinline__ bool plain_string_len(const ReduceSmem &W, uint32_t t
   return false;
 }
 
-__global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job *__restrict__ job) {
+// SH: the stage-2 tile is a stage-1 tile split in 2^SH (the run's s2_shift;
+// one kernel for each value, so that whole tiles pay no arithmetic for it).
+template <uint32_t SH>
+__device__ __forceinline__ void stage2_reduce(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ ReduceSmem WS[kS2Warps];
   __shared__ uint8_t s_kind[256];
@@ -304,8 +309,8 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
                   lane);
   for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
     tix.draw();  // the next tile, read at the loop's end
-    const uint32_t d = doc_of_tile(J, t);
-    const uint32_t j_min = J.tile_first[d];
+    const uint32_t d = doc_of_tile(J, t >> SH);
+    const uint32_t j_min = J.tile_first[d] << SH;
     const uint32_t tt = t - j_min;
     const uint32_t nidx = J.doc_nidx[d];
     if ((J.doc_flags[d] & kDocBad) || nidx == 0) {
@@ -316,22 +321,24 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job 
       continue;
     }
     if (lane == 0) J.s2_rec[t].s = 0;  // walks add to it, from this tile on
-    const uint32_t ntiles_d = J.tile_first[d + 1] - j_min;
+    const uint32_t ntiles_d = (J.tile_first[d + 1] << SH) - j_min;
+    constexpr uint32_t tblk = 32u >> SH;  // 64-byte blocks of a stage-2 tile
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
     const uint8_t *doc = J.base + J.doc_off[d];
     const uint64_t ib = idx_base(J, d);
     const uint32_t *idxp = J.idx + ib;
     const uint32_t cnt = J.tile_cnt[t], off = J.tile_off[t];
     uint32_t *slen = J.slen + ib + off;
-    const uint64_t t0 = (uint64_t)tt * kTileBytes;
+    const uint64_t t0 = (uint64_t)tt * (tblk * kBlockBytes);
+    constexpr uint32_t nstage = tblk * kBlockBytes + (kStageBytesR - kTileBytes);
     // masks of the tile's blocks and of the next ones in the document
-    const uint32_t nblk = min((uint32_t)kStageBlocksR, (ntiles_d - tt) * 32u);
+    const uint32_t nblk = min(nstage / kBlockBytes, (ntiles_d - tt) * tblk);
     for (uint32_t k = lane; k < nblk; k += 32) {
-      const ulonglong2 v = J.s1_qx[(uint64_t)t * 32 + k];
+      const ulonglong2 v = J.s1_qx[(uint64_t)t * tblk + k];
       W.q[k] = v.x;
       W.x[k] = v.y;
     }
-    const Staged sv = stage_tile<kStageBytesR>(W.bytes, doc, len, t0, lane);
+    const Staged sv = stage_tile<kStageBytesR>(W.bytes, doc, len, t0, lane, nstage);
     stg_lo = J.doc_off[d] + (uint64_t)sv.sbase;
     stg_hi = J.doc_off[d] + sv.slimit;
     const OpenTable ot = cnt < (uint32_t)kOpenSmem ? OpenTable{W.open, (uint32_t)kOpenSmem - 1u, 0}
@@ -511,7 +518,7 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
                   gridDim.x * (kNumThreads / 32), lane);
   for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
     tix.draw();
-    const uint32_t d = doc_of_tile(J, t);
+    const uint32_t d = s2_doc(J, t);
     if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
     const uint32_t m = J.tile_nnum[t] & ~kTileHasEscapes;
     if (m == 0) continue;
@@ -607,7 +614,8 @@ __device__ __forceinline__ void put_string_smem(uint8_t *__restrict__ o, uint32_
   dst[n] = 0;
 }
 
-__global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *__restrict__ job) {
+template <uint32_t SH>
+__device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ BuildSmem WS[kS2Warps];
   __shared__ uint16_t s_gram[32];
@@ -622,12 +630,14 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *
                   gridDim.x * kS2Warps, lane);
   for (uint32_t t = tix.first(); t < t_hi; t = tix.next()) {
     tix.draw();  // the next tile, read at the loop's end
-    const uint32_t d = doc_of_tile(J, t);
-    const uint32_t j_min = J.tile_first[d];
+    const uint32_t d = doc_of_tile(J, t >> SH);
+    const uint32_t j_min = J.tile_first[d] << SH;
     const uint32_t tt = t - j_min;
-    const uint32_t ntiles_d = J.tile_first[d + 1] - j_min;
+    const uint32_t ntiles_d = (J.tile_first[d + 1] << SH) - j_min;
     const uint32_t nidx = J.doc_nidx[d];
     if ((J.doc_flags[d] & kDocBad) || nidx == 0) continue;
+    constexpr uint32_t tbytes = kTileBytes >> SH;  // bytes of a stage-2 tile
+    constexpr uint32_t nstage = tbytes + (kStageBytesB - kTileBytes);
     const uint64_t len = J.doc_off[d + 1] - J.doc_off[d];
     const uint8_t *doc = J.base + J.doc_off[d];
     const uint64_t ib = idx_base(J, d);
@@ -659,7 +669,7 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *
     // starts inside, deepest first (levels d_start down to max(1, low))
     const uint32_t nfront = pre.d_start >= max(1, pre.low) ? (uint32_t)(pre.d_start - max(1, pre.low) + 1) : 0u;
     for (uint32_t k = lane; k < min(nfront, kFrontSmem); k += 32) W.front[k] = front[k];
-    const Staged sv = stage_tile<kStageBytesB>(W.bytes, doc, len, (uint64_t)tt * kTileBytes, lane);
+    const Staged sv = stage_tile<kStageBytesB>(W.bytes, doc, len, (uint64_t)tt * tbytes, lane, nstage);
     uint32_t shead = 0, stail = 0;
     const uint8_t *unesc = J.unesc + rel_off(J, d);
     // the scratch window, copied ahead when the tile has strings with escapes.
@@ -667,7 +677,7 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *
     // covers the same positions as the staged input (sv) in W.ubytes.
     const bool has_esc = (J.tile_nnum[t] & kTileHasEscapes) != 0 &&
                          (((uintptr_t)unesc ^ (uintptr_t)doc) & 15u) == 0;
-    if (has_esc) stage_tile_async<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * kTileBytes, lane);
+    if (has_esc) stage_tile_async<kStageBytesB>(W.ubytes, unesc, len, (uint64_t)tt * tbytes, lane, nstage);
     bool us_ready = !has_esc;
     uint64_t str_run = pre.str_start;  // buffer offset of the next queued string
 
@@ -927,7 +937,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(Job *job, const Job *hjob,
     J.counters[4] = 0;  // both stages: all tiles
     J.counters[5] = s_carry;
     J.counters[6] = 0;
-    J.counters[7] = s_carry;
+    J.counters[7] = s_carry << J.s2_shift;
     for (int k = kTicketReduce; k <= kTicketS1; k++) J.counters[k] = 0;
   }
 }
@@ -1001,6 +1011,19 @@ __global__ void finalize_kernel(const Job *__restrict__ job) {
     r.strings_offset = str_base(J, d);
     J.results[d] = r;
   }
+}
+
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job *__restrict__ job) {
+  stage2_reduce<0>(job);
+}
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_sub_kernel(const Job *__restrict__ job) {
+  stage2_reduce<kSmallShift>(job);
+}
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *__restrict__ job) {
+  stage2_build<0>(job);
+}
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_build_sub_kernel(const Job *__restrict__ job) {
+  stage2_build<kSmallShift>(job);
 }
 
 }  // namespace sj

@@ -197,7 +197,8 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
 }
 
 // The whole scan in one thread block, for parsers of at most kSmallTiles
-// tiles: the block walks the range in steps of kScanBlock tiles and carries
+// tiles (of the stage the scan serves): the block walks the range in steps of
+// kScanBlock tiles and carries
 // the inclusive prefix from one step to the next (the three launches above
 // cost more than they save on a few thousand tiles).  With SPT (stage 2) the
 // same block then builds the sparse table of tile minima in shared memory,
@@ -324,8 +325,8 @@ __global__ void jump_kernel(const Job *__restrict__ job) {
   s2_range(J, lo, n);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t t = lo + blockIdx.x * blockDim.x + threadIdx.x; t < n; t += stride) {
-    const uint32_t d = doc_of_tile(J, t);
-    const int64_t c = last_lower(J, (int64_t)t - 1, J.tile_first[d], J.s2_pre[t].low);
+    const uint32_t d = s2_doc(J, t);
+    const int64_t c = last_lower(J, (int64_t)t - 1, s2_first(J, d), J.s2_pre[t].low);
     J.s2_pre[t].jump = c < 0 ? kNoTile : (uint32_t)c;
   }
 }
@@ -347,8 +348,8 @@ __global__ void frontier_kernel(const Job *__restrict__ job) {
   const int lane = threadIdx.x & 31;
   const uint32_t nw = (gridDim.x * blockDim.x) >> 5;
   for (uint32_t t = t_lo + ((blockIdx.x * blockDim.x + threadIdx.x) >> 5); t < t_hi; t += nw) {
-    const uint32_t d = doc_of_tile(J, t);
-    const uint32_t j_min = J.tile_first[d];
+    const uint32_t d = s2_doc(J, t);
+    const uint32_t j_min = s2_first(J, d);
     if (J.doc_flags[d] & (kFlagUtf8 | kFlagUnclosed | kFlagCapacity)) continue;
     const S2Pre me = J.s2_pre[t];
     const int32_t lo = max(1, me.low), hi = me.d_start;

@@ -59,9 +59,14 @@ struct S2Pre {
   uint64_t str_start;
 };
 constexpr int kScanBlock = 1024;  // tiles per thread block in the tile scans
-// Parsers of at most this many tiles (4 MiB of input) scan in one thread
-// block and build the sparse table there; whole-document runs only.
+// Parsers of at most this many stage-2 tiles scan in one thread block and
+// build the sparse table there; whole-document runs only.
 constexpr uint32_t kSmallTiles = 2048;
+// Parsers of at most kSubTiles tiles (1 MiB of input) split each stage-1
+// tile in 2^kSmallShift stage-2 tiles (512 bytes) on whole-document runs, so
+// that a small document keeps four times the warps busy in stage 2.
+constexpr uint32_t kSmallShift = 2;
+constexpr uint32_t kSubTiles = kSmallTiles >> kSmallShift;
 // Runs of at most this many documents take the run descriptor and offsets
 // from pinned host memory in the set-up kernel and write their results
 // there (no copy operations in the run).
@@ -77,6 +82,10 @@ struct Job {
   const uint64_t *doc_off;  // n_docs + 1 byte offsets into base
   uint32_t n_docs;
   uint32_t max_depth;
+  // Stage-2 tiles are the stage-1 tiles split in 2^s2_shift (0 or 2): small
+  // whole-document runs split them so that a small document keeps more warps
+  // busy in the stage-2 passes.
+  uint32_t s2_shift;
   uint64_t max_doc_len;
   // scratch
   uint32_t *tile_first;     // n_docs + 1: first stage-1 tile of each document
@@ -182,6 +191,15 @@ __device__ __forceinline__ uint32_t doc_of_tile(const Job &J, uint32_t t) {
     if (J.tile_first[mid] <= t) lo = mid; else hi = mid;
   }
   return lo;
+}
+
+// Stage-2 tiles (2^s2_shift per stage-1 tile): the document owning stage-2
+// tile t, and the first stage-2 tile of document d.
+__device__ __forceinline__ uint32_t s2_doc(const Job &J, uint32_t t) {
+  return doc_of_tile(J, t >> J.s2_shift);
+}
+__device__ __forceinline__ uint32_t s2_first(const Job &J, uint32_t d) {
+  return J.tile_first[d] << J.s2_shift;
 }
 
 // ---- memory-ordering helpers for the decoupled look-back ----------------
