@@ -161,7 +161,7 @@ uint64_t sj_parser_device_bytes(const sj_parser *p);
  * several batches are on the GPU at once.  Results stay in the slot's device
  * buffers until every document of the batch has been released.  Slots are
  * created, up to max_slots, while their device memory fits mem_budget
- * (0 = no budget).  Each slot also holds a small parser (1 MiB, 64
+ * (0 = no budget).  Each slot also holds a small parser (768 KiB, 64
  * documents, counted in the budget) that runs the batches within those
  * limits with fewer launches.  Not thread-safe: one host thread drives a
  * server. */

@@ -25,9 +25,10 @@
 namespace {
 
 // Small batches (the common case at moderate load) run on a second, small
-// parser of the slot: a parser for at most 2048 tiles runs 11 launches per
-// batch instead of 18 (one-block tile scans).
-constexpr uint64_t kSmallBatchBytes = 1ull << 20;
+// parser of the slot: a parser of at most 512 tiles runs 11 launches per batch
+// instead of 18 (one-block tile scans) and splits each tile in four for stage
+// 2, so that a batch of a few small documents keeps more warps busy.
+constexpr uint64_t kSmallBatchBytes = 768ull << 10;
 constexpr uint32_t kSmallBatchDocs = 64;
 
 struct Slot {

@@ -90,7 +90,11 @@ def test_each_result_same_alone_and_in_the_mix():
 
 def test_admission_follows_the_memory_budget():
     import paper_1902_08318_gb300 as sj
-    one = sj.Parser(max_bytes=1 << 20, max_docs=16).device_bytes()
+    # a slot's device memory (its parsers), as the server counts it
+    probe = sj.Server(max_batch_bytes=1 << 20, max_batch_docs=16, max_slots=1, mem_budget=0)
+    one = probe.device_bytes
+    probe.close()
+    assert one >= sj.Parser(max_bytes=1 << 20, max_docs=16).device_bytes()
     srv = sj.Server(max_batch_bytes=1 << 20, max_batch_docs=16, max_slots=8,
                     mem_budget=int(2.5 * one))
     assert srv.slots == 2
