@@ -388,7 +388,7 @@ def report(args, world, desc, B, S, T, SB, lex, nnum, ms_step, stage_ms, ms_e2e,
         "stage_ms": {k: round(v, 4) for k, v in stage_ms.items()},
         "e2e": {"value": round(e2e, 3) if e2e == e2e else None, "unit": "GB/s",
                 "h2d_bytes_per_step": B, "d2h_bytes_per_step": 56,
-                "path": ("pinned host document copied in chunks (first 32 MiB, doubling up to "
+                "path": ("pinned host document copied in chunks (first 32 MiB, growing by 7/4 up to "
                          "512 MiB) on a copy stream; stage 1 of each landed chunk on a second "
                          "stream, stage 2 on the run's stream as far as the landed chunks allow"
                          if B > (512 << 20) else
