@@ -19,8 +19,10 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   parse        pinned: Fig. 1 -> Fig. "jsontape" (all 38 words), accept/reject
                vs Python's json on every document of <= 5 bytes over a reduced
                alphabet, numbers vs Python's float/int, invariants.
-               The error *category* among several failures is pinned by
-               hand-written cases only ("parity unpinned" beyond them).
+               Error categories: single defects injected into valid
+               documents and ordered pairs of defects (categories fixed by
+               construction); several defects at one token stay "parity
+               unpinned".
 """
 from __future__ import annotations
 
