@@ -29,6 +29,7 @@ __global__ void stage2_reduce_sub_kernel(const Job *job);
 __global__ void stage2_build_kernel(const Job *job);
 __global__ void stage2_build_sub_kernel(const Job *job);
 __global__ void numbers_kernel(const Job *job);
+__global__ void numbers_split_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
 __global__ void spt_build_kernel(const Job *job, uint32_t src);
 __global__ void jump_kernel(const Job *job);
@@ -38,7 +39,8 @@ __global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, i
 void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
 void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
 void launch_scan1_small(const Job *job, cudaStream_t s);
-void launch_scan2_spt_small(const Job *job, cudaStream_t s);
+void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s);
+cudaError_t prepare_scan2_spt_small(size_t spt_smem);
 }  // namespace sj
 
 using sj::Job;
@@ -99,6 +101,7 @@ struct sj_parser {
   // at most kSmallTiles stage-2 tiles: one-block scans, sparse table built
   // with scan 2; with `sub`, stage-2 tiles of a quarter on whole runs
   bool small = false, sub = false;
+  size_t spt_smem = 0;  // small: the one-block sparse table's shared memory
   // launch shapes
   int s1_grid = 0, fl_grid = 0, s2r_grid = 0, s2b_grid = 0, fin_grid = 0, aux_grid = 0;
   // The most blocks a launch can use: the kernels loop over tiles (4 per
@@ -223,6 +226,12 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_scan_agg1, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_scan_pre1, p->scan_blocks))) return r;
   if ((r = dalloc(p, &p->d_spt, (uint64_t)p->spt_levels * tiles2))) return r;
+  if (p->small) {
+    p->spt_smem = (size_t)p->spt_levels * tiles2 * sizeof(int32_t);
+    // the limit of the function, for every parser alike: the largest table
+    // (13 levels of kSmallTiles)
+    CK(sj::prepare_scan2_spt_small((size_t)13 * sj::kSmallTiles * sizeof(int32_t)));
+  }
   if ((r = dalloc(p, &p->d_slen, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
@@ -380,6 +389,16 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
 // beside the scan and frontier kernels, joined before the build pass.
 // `whole`: the run covers whole documents from tile 0 (not a round of a
 // chunked run), so a small parser may build the sparse table with scan 2.
+// Small whole runs give each tile four warps (32 numbers each, the last
+// warp the rest); other runs queue numbers per warp across the tiles it draws.
+static void launch_numbers(sj_parser *p, cudaStream_t s, bool whole) {
+  if (p->small && whole) {
+    sj::numbers_split_kernel<<<p->tile_blocks * 4, 128, 0, s>>>(p->d_job);
+    return;
+  }
+  sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
+}
+
 static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole) {
   const bool sub = p->sub && whole;  // the run's s2_shift
   if (sub)
@@ -390,20 +409,20 @@ static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool w
   if (!ev) {
     cudaEventRecord(p->ev_fork, s);
     cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
-    sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, p->aux_stream>>>(p->d_job);
+    launch_numbers(p, p->aux_stream, whole);
     cudaEventRecord(p->ev_join, p->aux_stream);
   }
   if (p->small && whole) {
-    sj::launch_scan2_spt_small(p->d_job, s);
+    sj::launch_scan2_spt_small(p->d_job, p->spt_smem, s);  // scan, sparse table, jump pointers
   } else {
     sj::launch_scan2(p->d_job, p->scan_grid, s);
     for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
       sj::spt_build_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job, src);
+    sj::jump_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   }
-  sj::jump_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   sj::frontier_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[6], s);
-  if (ev) sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
+  if (ev) launch_numbers(p, s, whole);
   else cudaStreamWaitEvent(s, p->ev_join, 0);
   if (ev) cudaEventRecord(ev[7], s);
   if (sub)
@@ -428,8 +447,8 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool zc, 
 
 static uint32_t kernels_per_run(const sj_parser *p) {
   if (p->small)
-    return 2 /* setup, blocks */ + 1 + 1 /* scan1, flatten */ + 1 + 1 /* reduce, scan2 and
-         sparse table */ + 2 /* jump, frontier */ + 1 /* numbers */ + 1 + 1 /* build, finalize */;
+    return 2 /* setup, blocks */ + 1 + 1 /* scan1, flatten */ + 1 + 1 /* reduce; scan2, sparse
+         table and jump pointers */ + 1 /* frontier */ + 1 /* numbers */ + 1 + 1 /* build, finalize */;
   return 2 /* setup, blocks */ + 3 + 1 /* scan1, flatten */ + 1 + 3 /* reduce, scan2 */ +
          (p->spt_levels + 2) / 4 + 2 /* sparse table, jump, frontier */ + 1 /* numbers */ +
          1 + 1 /* build, finalize */;

@@ -471,18 +471,9 @@ struct NumEntry {
 };
 // 12 resident blocks (40 registers): the kernel waits on scattered lexeme
 // loads, so more warps in flight beat the few spilled registers.
-__global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__restrict__ job) {
-  const Job &J = *job;
-  __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
-  __shared__ NumEntry q[kNumThreads / 32][64];
-  const int lane = threadIdx.x & 31;
-  uint8_t *my = win[threadIdx.x];
-  NumEntry *wq = q[threadIdx.x >> 5];
-  uint32_t head = 0, tail = 0;
-  auto flush = [&]() {
-    const uint32_t m = min(32u, tail - head);
-    if ((uint32_t)lane < m) {
-      const NumEntry e = wq[(head + lane) & 63u];
+// One number token: its lexeme window staged in `my` (kNumWindow + 16
+// bytes of shared memory), converted; value and tag (or error) stored.
+__device__ __forceinline__ void convert_number(const Job &J, const NumEntry &e, uint8_t *my) {
       const uint64_t len = J.doc_off[e.d + 1] - J.doc_off[e.d];
       const uint8_t *doc = J.base + J.doc_off[e.d];
       const uint32_t nidx = J.doc_nidx[e.d];
@@ -508,7 +499,19 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
         J.slen[e.slot] = tag;
         J.numv[e.slot] = v;
       }
-    }
+}
+
+__global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__restrict__ job) {
+  const Job &J = *job;
+  __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
+  __shared__ NumEntry q[kNumThreads / 32][64];
+  const int lane = threadIdx.x & 31;
+  uint8_t *my = win[threadIdx.x];
+  NumEntry *wq = q[threadIdx.x >> 5];
+  uint32_t head = 0, tail = 0;
+  auto flush = [&]() {
+    const uint32_t m = min(32u, tail - head);
+    if ((uint32_t)lane < m) convert_number(J, wq[(head + lane) & 63u], my);
     head += m;
     __syncwarp();
   };
@@ -537,6 +540,37 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
     }
   }
   while (head != tail) flush();
+}
+
+// The same conversion for small runs, where a warp per tile leaves a
+// number-heavy tile's numbers to one warp in turn: warp w of the grid takes
+// group w % kNumGroups of tile w / kNumGroups -- numbers 32g to 32g + 31 of
+// the tile's list, the last group all from there on -- so up to kNumGroups
+// warps share a tile.
+constexpr uint32_t kNumGroups = 4;
+__global__ void __launch_bounds__(kNumThreads, 12) numbers_split_kernel(const Job *__restrict__ job) {
+  const Job &J = *job;
+  __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
+  const int lane = threadIdx.x & 31;
+  uint8_t *my = win[threadIdx.x];
+  uint32_t t_lo, t_hi;
+  s2_range(J, t_lo, t_hi);
+  const uint32_t gw = blockIdx.x * (kNumThreads / 32) + (threadIdx.x >> 5);
+  const uint32_t nw = gridDim.x * (kNumThreads / 32);
+  for (uint32_t w = gw; w < (t_hi - t_lo) * kNumGroups; w += nw) {
+    const uint32_t t = t_lo + w / kNumGroups, g = w % kNumGroups;
+    const uint32_t d = s2_doc(J, t);
+    if ((J.doc_flags[d] & kDocBad) || J.doc_nidx[d] == 0) continue;
+    const uint32_t m = J.tile_nnum[t] & ~kTileHasEscapes;
+    const uint32_t k0 = 32u * g, k1 = g + 1 == kNumGroups ? m : min(m, k0 + 32u);
+    if (k0 >= k1) continue;
+    const uint64_t ib = idx_base(J, d);
+    const uint32_t off = J.tile_off[t];
+    for (uint32_t k = k0 + lane; k < k1; k += 32) {
+      const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
+      convert_number(J, NumEntry{ib + rel, d, rel}, my);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------

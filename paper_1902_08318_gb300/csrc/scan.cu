@@ -203,7 +203,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
 // cost more than they save on a few thousand tiles).  With SPT (stage 2) the
 // same block then builds the sparse table of tile minima in shared memory,
 // one level from the one before (level k: minimum over the 2^k tiles ending
-// at a tile), and writes every level out.
+// at a tile), and the jump pointers from it (no jump_kernel launch).
 template <class M, bool SPT>
 __global__ void __launch_bounds__(kScanBlock) scan_single_kernel(const Job *__restrict__ job) {
   using T = typename M::T;
@@ -211,7 +211,6 @@ __global__ void __launch_bounds__(kScanBlock) scan_single_kernel(const Job *__re
   __shared__ T s_warp[32];
   __shared__ T s_incl[kScanBlock];
   __shared__ T s_carry;
-  __shared__ int32_t s_low[2][SPT ? kSmallTiles : 1];
   uint32_t lo, n;
   M::range(J, lo, n);
   if (threadIdx.x == 0)
@@ -235,23 +234,30 @@ __global__ void __launch_bounds__(kScanBlock) scan_single_kernel(const Job *__re
     __syncthreads();
   }
   if constexpr (SPT) {
-    // whole-document runs only (lo == 0, n <= kSmallTiles)
-    for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) {
-      const int32_t v = J.s2_pre[t].low;
-      s_low[0][t] = v;
-      J.spt[t] = v;
-    }
+    // Whole-document runs only (lo == 0, n <= kSmallTiles).  Every level of
+    // the sparse table stays in shared memory (dynamic: spt_levels rows of
+    // n), and each tile's jump pointer is found there by binary lifting, as
+    // jump_kernel does from the table in global memory.
+    extern __shared__ int32_t s_spt[];
+    for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) s_spt[t] = J.s2_pre[t].low;
     __syncthreads();
     for (uint32_t k = 1; k < J.spt_levels; k++) {
-      const int32_t *in = s_low[(k - 1) & 1];
-      int32_t *out = s_low[k & 1];
+      const int32_t *in = s_spt + (k - 1) * n;
+      int32_t *out = s_spt + k * n;
       const uint32_t step = 1u << (k - 1);
-      for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) {
-        const int32_t v = t >= step ? min(in[t], in[t - step]) : in[t];
-        out[t] = v;
-        J.spt[(uint64_t)k * J.spt_stride + t] = v;
-      }
+      for (uint32_t t = threadIdx.x; t < n; t += kScanBlock)
+        out[t] = t >= step ? min(in[t], in[t - step]) : in[t];
       __syncthreads();
+    }
+    for (uint32_t t = threadIdx.x; t < n; t += kScanBlock) {
+      const int64_t lo_d = s2_first(J, s2_doc(J, t));
+      const int32_t x = s_spt[t];
+      int64_t c = (int64_t)t - 1;
+      for (int k = (int)J.spt_levels - 1; k >= 0 && c >= lo_d; k--) {
+        const int64_t w = 1ll << k;
+        if (c - w + 1 >= lo_d && s_spt[(uint32_t)k * n + (uint32_t)c] >= x) c -= w;
+      }
+      J.s2_pre[t].jump = c >= lo_d ? (uint32_t)c : kNoTile;
     }
   }
 }
@@ -279,8 +285,13 @@ void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s) {
 void launch_scan1_small(const Job *job, cudaStream_t s) {
   scan_single_kernel<M1, false><<<1, kScanBlock, 0, s>>>(job);
 }
-void launch_scan2_spt_small(const Job *job, cudaStream_t s) {
-  scan_single_kernel<M2, true><<<1, kScanBlock, 0, s>>>(job);
+void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s) {
+  scan_single_kernel<M2, true><<<1, kScanBlock, spt_smem, s>>>(job);
+}
+// The sparse table in shared memory may exceed a launch's default limit.
+cudaError_t prepare_scan2_spt_small(size_t spt_smem) {
+  return cudaFuncSetAttribute(scan_single_kernel<M2, true>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)spt_smem);
 }
 
 // ---- nearest earlier tile with a lower `low` -----------------------------------

@@ -25,7 +25,7 @@
 namespace {
 
 // Small batches (the common case at moderate load) run on a second, small
-// parser of the slot: a parser of at most 512 tiles runs 11 launches per batch
+// parser of the slot: a parser of at most 512 tiles runs 10 launches per batch
 // instead of 18 (one-block tile scans) and splits each tile in four for stage
 // 2, so that a batch of a few small documents keeps more warps busy.
 constexpr uint64_t kSmallBatchBytes = 768ull << 10;
