@@ -36,10 +36,10 @@ __global__ void jump_kernel(const Job *job);
 __global__ void frontier_kernel(const Job *job);
 __global__ void chunk_range_kernel(const Job *job, uint32_t lo1, uint32_t hi1, int mode,
                                    uint32_t c, int last);
-void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s);
-void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s);
-void launch_scan1_small(const Job *job, cudaStream_t s);
-void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s);
+void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s, bool pdl);
+void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s, bool pdl);
+void launch_scan1_small(const Job *job, cudaStream_t s, bool pdl);
+void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s, bool pdl);
 cudaError_t prepare_scan2_spt_small(size_t spt_smem);
 }  // namespace sj
 
@@ -372,14 +372,21 @@ extern "C" sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint3
 static inline int cap(int grid, int most) { return grid < most ? grid : most; }
 
 // The kernels of one run, in order.  With `ev`, an event is recorded before
-// the first kernel and after each of the stages named in STAGE_NAMES.
-static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev) {
-  sj::stage1_blocks_kernel<<<cap(p->s1_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+// the first kernel and after each of the stages named in STAGE_NAMES.  With
+// `pdl` a kernel that follows another kernel on the same stream is launched
+// with programmatic stream serialization (sj::launch_k), so that it is
+// launched as soon as the blocks of the one before have exited; every run
+// uses it but the profiled runs, whose events between kernels time each
+// stage alone.
+static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool pdl) {
+  sj::launch_k(pdl, sj::stage1_blocks_kernel, cap(p->s1_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s,
+               (const Job *)p->d_job);
   if (ev) cudaEventRecord(ev[2], s);
-  if (p->small) sj::launch_scan1_small(p->d_job, s);
-  else sj::launch_scan1(p->d_job, p->scan_grid, s);
+  if (p->small) sj::launch_scan1_small(p->d_job, s, pdl);
+  else sj::launch_scan1(p->d_job, p->scan_grid, s, pdl);
   if (ev) cudaEventRecord(ev[3], s);
-  sj::stage1_flatten_kernel<<<cap(p->fl_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s>>>(p->d_job);
+  sj::launch_k(pdl, sj::stage1_flatten_kernel, cap(p->fl_grid, p->tile_blocks), 32 * sj::kS1Warps, 0, s,
+               (const Job *)p->d_job);
   if (ev) cudaEventRecord(ev[4], s);
 }
 
@@ -399,12 +406,11 @@ static void launch_numbers(sj_parser *p, cudaStream_t s, bool whole) {
   sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
 }
 
-static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole) {
+static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole, bool pdl) {
   const bool sub = p->sub && whole;  // the run's s2_shift
-  if (sub)
-    sj::stage2_reduce_sub_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
-  else
-    sj::stage2_reduce_kernel<<<cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+  const Job *job = p->d_job;
+  sj::launch_k(pdl, sub ? sj::stage2_reduce_sub_kernel : sj::stage2_reduce_kernel,
+               cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s, job);
   if (ev) cudaEventRecord(ev[5], s);
   if (!ev) {
     cudaEventRecord(p->ev_fork, s);
@@ -413,14 +419,14 @@ static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool w
     cudaEventRecord(p->ev_join, p->aux_stream);
   }
   if (p->small && whole) {
-    sj::launch_scan2_spt_small(p->d_job, p->spt_smem, s);  // scan, sparse table, jump pointers
+    sj::launch_scan2_spt_small(job, p->spt_smem, s, pdl);  // scan, sparse table, jump pointers
   } else {
-    sj::launch_scan2(p->d_job, p->scan_grid, s);
+    sj::launch_scan2(job, p->scan_grid, s, pdl);
     for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
-      sj::spt_build_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job, src);
-    sj::jump_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
+      sj::launch_k(pdl, sj::spt_build_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job, src);
+    sj::launch_k(pdl, sj::jump_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job);
   }
-  sj::frontier_kernel<<<cap(p->aux_grid, p->aux_blocks), 256, 0, s>>>(p->d_job);
+  sj::launch_k(pdl, sj::frontier_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job);
   if (ev) cudaEventRecord(ev[6], s);
   if (ev) launch_numbers(p, s, whole);
   else cudaStreamWaitEvent(s, p->ev_join, 0);
@@ -439,9 +445,10 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool zc, 
   sj::setup_kernel<<<1, 1024, 0, s>>>(p->d_job, zc ? p->h_job_dev : nullptr,
                                       zc ? p->h_doc_off_dev : nullptr, zc ? n_off : 0u);
   if (ev) cudaEventRecord(ev[1], s);
-  enqueue_stage1(p, s, ev);
-  enqueue_stage2(p, s, ev, true);
-  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
+  const bool pdl = !ev;
+  enqueue_stage1(p, s, ev, pdl);
+  enqueue_stage2(p, s, ev, true, pdl);
+  sj::launch_k(pdl, sj::finalize_kernel, cap(p->fin_grid, p->doc_blocks), 256, 0, s, (const Job *)p->d_job);
   if (ev) cudaEventRecord(ev[9], s);
 }
 
@@ -579,16 +586,16 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
     CK(cudaStreamWaitEvent(p->s1_stream, p->ev_chunk[c], 0));
     sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(
         p->d_job, (uint32_t)(at[c] / tile), (uint32_t)((at[c + 1] + tile - 1) / tile), 0, c, 0);
-    enqueue_stage1(p, p->s1_stream, nullptr);
-    sj::chunk_range_kernel<<<1, 32, 0, p->s1_stream>>>(p->d_job, 0, 0, 1, c, 0);
+    enqueue_stage1(p, p->s1_stream, nullptr, true);
+    sj::launch_k(true, sj::chunk_range_kernel, 1, 32, 0, p->s1_stream, (const Job *)p->d_job, 0u, 0u, 1, c, 0);
     CK(cudaEventRecord(p->ev_s1[c], p->s1_stream));
   }
   for (uint32_t c = 0; c < nc; c++) {
     CK(cudaStreamWaitEvent(s, p->ev_s1[c], 0));
     sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
-    enqueue_stage2(p, s, nullptr, false);
+    enqueue_stage2(p, s, nullptr, false, true);
   }
-  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
+  sj::launch_k(true, sj::finalize_kernel, cap(p->fin_grid, p->doc_blocks), 256, 0, s, (const Job *)p->d_job);
   CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   return SJ_SUCCESS;

@@ -97,6 +97,7 @@ __device__ __forceinline__ bool utf8_block_error_masks(const uint32_t (&w)[16], 
 enum : uint32_t { kSepNever = 0, kSepAlways = 1, kSepIfOutside = 2 };
 
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   __shared__ uint32_t s_words[kS1Warps * 32][16];  // one block per thread (byte reads)
   const int lane = threadIdx.x & 31;
@@ -233,6 +234,7 @@ __global__ void __launch_bounds__(32 * kS1Warps) stage1_blocks_kernel(const Job 
 // and write the indices (Sec. 3.1.4) at the tile's offset, staged in shared
 // memory so that the stores are coalesced.
 __global__ void __launch_bounds__(32 * kS1Warps) stage1_flatten_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   const int lane = threadIdx.x & 31;
 #ifndef SJ_ABL_NAIVE_FLATTEN

@@ -502,6 +502,7 @@ __device__ __forceinline__ void convert_number(const Job &J, const NumEntry &e, 
 }
 
 __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
   __shared__ NumEntry q[kNumThreads / 32][64];
@@ -549,6 +550,7 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
 // warps share a tile.
 constexpr uint32_t kNumGroups = 4;
 __global__ void __launch_bounds__(kNumThreads, 12) numbers_split_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   __shared__ __align__(16) uint8_t win[kNumThreads][kNumWindow + 16];
   const int lane = threadIdx.x & 31;
@@ -911,6 +913,7 @@ __device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
 // the descriptor's doc_off): a small run then needs no copy operation.
 __global__ void __launch_bounds__(1024) setup_kernel(Job *job, const Job *hjob,
                                                      const uint64_t *hoff, uint32_t n_off) {
+  pdl_enter();
   static_assert(sizeof(Job) % 4 == 0, "the descriptor is copied in words");
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   if (hjob) {
@@ -989,6 +992,7 @@ __global__ void __launch_bounds__(1024) setup_kernel(Job *job, const Job *hjob,
 // another stream meanwhile and moves the running index count.
 __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, uint32_t hi1,
                                    int mode, uint32_t c, int last) {
+  pdl_enter();
   const Job &J = *job;
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
   if (mode == 0) {
@@ -1022,6 +1026,7 @@ __global__ void chunk_range_kernel(const Job *__restrict__ job, uint32_t lo1, ui
 // Per-document results (error precedence: capacity, empty, UTF-8, unclosed
 // string, internal, then the first failing token).
 __global__ void finalize_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t d = blockIdx.x * blockDim.x + threadIdx.x; d < J.n_docs; d += stride) {
@@ -1048,15 +1053,19 @@ __global__ void finalize_kernel(const Job *__restrict__ job) {
 }
 
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   stage2_reduce<0>(job);
 }
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_sub_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   stage2_reduce<kSmallShift>(job);
 }
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   stage2_build<0>(job);
 }
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_sub_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   stage2_build<kSmallShift>(job);
 }
 

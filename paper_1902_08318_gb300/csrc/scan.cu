@@ -121,6 +121,7 @@ __device__ typename M::T block_inclusive(typename M::T v, typename M::T *s_warp,
 // few blocks per SM serves a whole document or one chunk of it alike.
 template <class M>
 __global__ void __launch_bounds__(kScanBlock) scan_up_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   using T = typename M::T;
   const Job &J = *job;
   __shared__ T s_warp[32];
@@ -137,6 +138,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_up_kernel(const Job *__restri
 
 template <class M>
 __global__ void __launch_bounds__(kScanBlock) scan_top_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   using T = typename M::T;
   const Job &J = *job;
   __shared__ T s_warp[32];
@@ -169,6 +171,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_top_kernel(const Job *__restr
 
 template <class M>
 __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   using T = typename M::T;
   const Job &J = *job;
   __shared__ T s_warp[32];
@@ -206,6 +209,7 @@ __global__ void __launch_bounds__(kScanBlock) scan_down_kernel(const Job *__rest
 // at a tile), and the jump pointers from it (no jump_kernel launch).
 template <class M, bool SPT>
 __global__ void __launch_bounds__(kScanBlock) scan_single_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   using T = typename M::T;
   const Job &J = *job;
   __shared__ T s_warp[32];
@@ -272,21 +276,21 @@ template __global__ void scan_up_kernel<M2>(const Job *);
 template __global__ void scan_top_kernel<M2>(const Job *);
 template __global__ void scan_down_kernel<M2>(const Job *);
 
-void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s) {
-  scan_up_kernel<M1><<<blocks, kScanBlock, 0, s>>>(job);
-  scan_top_kernel<M1><<<1, kScanBlock, 0, s>>>(job);
-  scan_down_kernel<M1><<<blocks, kScanBlock, 0, s>>>(job);
+void launch_scan1(const Job *job, uint32_t blocks, cudaStream_t s, bool pdl) {
+  launch_k(pdl, scan_up_kernel<M1>, blocks, kScanBlock, 0, s, job);
+  launch_k(pdl, scan_top_kernel<M1>, 1, kScanBlock, 0, s, job);
+  launch_k(pdl, scan_down_kernel<M1>, blocks, kScanBlock, 0, s, job);
 }
-void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s) {
-  scan_up_kernel<M2><<<blocks, kScanBlock, 0, s>>>(job);
-  scan_top_kernel<M2><<<1, kScanBlock, 0, s>>>(job);
-  scan_down_kernel<M2><<<blocks, kScanBlock, 0, s>>>(job);
+void launch_scan2(const Job *job, uint32_t blocks, cudaStream_t s, bool pdl) {
+  launch_k(pdl, scan_up_kernel<M2>, blocks, kScanBlock, 0, s, job);
+  launch_k(pdl, scan_top_kernel<M2>, 1, kScanBlock, 0, s, job);
+  launch_k(pdl, scan_down_kernel<M2>, blocks, kScanBlock, 0, s, job);
 }
-void launch_scan1_small(const Job *job, cudaStream_t s) {
-  scan_single_kernel<M1, false><<<1, kScanBlock, 0, s>>>(job);
+void launch_scan1_small(const Job *job, cudaStream_t s, bool pdl) {
+  launch_k(pdl, scan_single_kernel<M1, false>, 1, kScanBlock, 0, s, job);
 }
-void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s) {
-  scan_single_kernel<M2, true><<<1, kScanBlock, spt_smem, s>>>(job);
+void launch_scan2_spt_small(const Job *job, size_t spt_smem, cudaStream_t s, bool pdl) {
+  launch_k(pdl, scan_single_kernel<M2, true>, 1, kScanBlock, spt_smem, s, job);
 }
 // The sparse table in shared memory may exceed a launch's default limit.
 cudaError_t prepare_scan2_spt_small(size_t spt_smem) {
@@ -298,6 +302,7 @@ cudaError_t prepare_scan2_spt_small(size_t spt_smem) {
 // Sparse table of minima: level k holds min(low[t - 2^k + 1 .. t]).  Each
 // launch derives four levels from level `src` (sixteen reads per tile).
 __global__ void spt_build_kernel(const Job *__restrict__ job, uint32_t src) {
+  pdl_enter();
   const Job &J = *job;
   uint32_t lo, n;
   s2_range(J, lo, n);
@@ -331,6 +336,7 @@ __device__ __forceinline__ int64_t last_lower(const Job &J, int64_t from, int64_
 }
 
 __global__ void jump_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   uint32_t lo, n;
   s2_range(J, lo, n);
@@ -353,6 +359,7 @@ __global__ void jump_kernel(const Job *__restrict__ job) {
 // so the warp walks the chain of those tiles (jump pointers) once and copies
 // each range with all lanes.
 __global__ void frontier_kernel(const Job *__restrict__ job) {
+  pdl_enter();
   const Job &J = *job;
   uint32_t t_lo, t_hi;
   s2_range(J, t_lo, t_hi);

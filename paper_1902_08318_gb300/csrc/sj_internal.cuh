@@ -26,6 +26,34 @@ constexpr uint32_t kSpinLimit = SJ_SPIN_LIMIT;
 constexpr uint32_t kSpinLimit = 1u << 24;
 #endif
 
+// Programmatic dependent launch.  The kernels of a run after the first may be
+// launched with programmatic stream serialization (launch_k with pdl): the
+// GPU then launches a kernel as soon as every block of the kernel ahead of it
+// in the stream has exited, without waiting for that kernel's completion to
+// be signalled, and the kernel's first act, pdl_enter(), waits until the
+// kernel ahead has completed and its writes are visible.  The results are
+// those of plain launches; what overlaps is each launch with the end of the
+// kernel before.  No kernel triggers its dependents early: blocks of the next
+// kernel resident and waiting beside a running kernel made the 1 GiB parse
+// 3% slower.  Without the attribute the wait does nothing.
+__device__ __forceinline__ void pdl_enter() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... P, typename... A>
+inline void launch_k(bool pdl, void (*k)(P...), unsigned grid, unsigned block, size_t smem,
+                     cudaStream_t s, A... a) {
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t c = {};
+  c.gridDim = dim3(grid);
+  c.blockDim = dim3(block);
+  c.dynamicSmemBytes = smem;
+  c.stream = s;
+  c.attrs = at;
+  c.numAttrs = pdl ? 1 : 0;
+  cudaLaunchKernelEx(&c, k, a...);
+}
+
 // Per-document flags written by the kernels.
 constexpr uint32_t kFlagUtf8 = 1, kFlagUnclosed = 2, kFlagInternal = 4, kFlagCapacity = 8;
 
