@@ -108,8 +108,9 @@ typedef struct {
 /* Create a parser for inputs of at most max_bytes bytes in total (summed over
  * a batch) and at most max_docs documents per batch (0 = 1).  max_depth is
  * the nesting limit (0 = 4096; at most 4096); the root container has depth 1.
- * Allocates all device memory up front (about 53 bytes per input byte, plus
- * about 35 MB of per-warp tables; sj_parser_device_bytes tells the total).
+ * Allocates all device memory up front (about 45 bytes per input byte, 53
+ * for a parser of at most 4 MiB, plus about 35 MB of per-warp tables;
+ * sj_parser_device_bytes tells the total).
  * Returns SJ_SUCCESS and *out, or an error status and *out = NULL. */
 sj_status sj_parser_create(sj_parser **out, uint64_t max_bytes, uint32_t max_docs,
                            uint32_t max_depth);

@@ -28,6 +28,7 @@ __global__ void stage2_reduce_kernel(const Job *job);
 __global__ void stage2_reduce_sub_kernel(const Job *job);
 __global__ void stage2_build_kernel(const Job *job);
 __global__ void stage2_build_sub_kernel(const Job *job);
+__global__ void stage2_build_small_kernel(const Job *job);
 __global__ void numbers_kernel(const Job *job);
 __global__ void numbers_split_kernel(const Job *job);
 __global__ void finalize_kernel(const Job *job);
@@ -75,8 +76,8 @@ struct sj_parser {
   uint64_t *d_meta = nullptr;
   uint16_t *d_open_g = nullptr;
   uint8_t *d_unesc = nullptr;
-  uint64_t *d_numv = nullptr;
   uint32_t *d_nlist = nullptr;
+  uint64_t *d_numv = nullptr;  // small parsers only
   uint32_t *d_tile_nnum = nullptr;
   uint64_t *d_front = nullptr;
   uint32_t *d_surv = nullptr;
@@ -183,7 +184,7 @@ extern "C" void sj_parser_destroy(sj_parser *p) {
                  p->d_scan_agg, p->d_scan_pre, p->d_scan_agg1, p->d_scan_pre1, p->d_spt, p->d_slen, p->d_front, p->d_surv,
                  p->d_idx, p->d_tape, p->d_strings, p->d_doc_flags, p->d_doc_nidx, p->d_doc_err,
                  p->d_doc_tape, p->d_doc_str, p->d_results, p->d_job, p->d_s1_qx, p->d_meta,
-                 p->d_open_g, p->d_unesc, p->d_numv, p->d_nlist, p->d_tile_nnum};
+                 p->d_open_g, p->d_unesc, p->d_nlist, p->d_numv, p->d_tile_nnum};
   for (void *q : dev)
     if (q) cudaFree(q);
   if (p->h_job) cudaFreeHost(p->h_job);
@@ -236,8 +237,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   if ((r = dalloc(p, &p->d_s1_qx, tiles * 32))) return r;
   if ((r = dalloc(p, &p->d_meta, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_unesc, max_bytes + 64 + 16))) return r;
-  if ((r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;
   if ((r = dalloc(p, &p->d_nlist, max_bytes + 16))) return r;
+  if (p->small && (r = dalloc(p, &p->d_numv, max_bytes + 16))) return r;  // per index slot
   if ((r = dalloc(p, &p->d_tile_nnum, tiles2))) return r;
   if ((r = dalloc(p, &p->d_front, max_bytes + tiles2 + 16))) return r;
   if ((r = dalloc(p, &p->d_surv, max_bytes + 16))) return r;
@@ -334,8 +335,8 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   J.meta = p->d_meta;
   J.open_g = p->d_open_g;
   J.unesc = p->d_unesc;
-  J.numv = p->d_numv;
   J.nlist = p->d_nlist;
+  J.numv = p->d_numv;
   J.tile_nnum = p->d_tile_nnum;
   J.front = p->d_front;
   J.surv = p->d_surv;
@@ -390,52 +391,59 @@ static void enqueue_stage1(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool p
   if (ev) cudaEventRecord(ev[4], s);
 }
 
-// Stage 2.  The number conversions need only the reduce pass, and the tile
-// scan and frontier do not touch their data, so (except in profiled runs,
-// which time each stage alone) the numbers kernel runs on a second stream
-// beside the scan and frontier kernels, joined before the build pass.
+// Stage 2.  numbers_kernel needs the reduce pass's number lists and the tile
+// scan's first tape slots, and writes only its tokens' tape words and
+// errors, so (except in profiled runs, which time each stage alone) it runs
+// on a second stream from the tile scan on, beside the sparse-table,
+// frontier and build kernels, joined after the build pass.  Small whole runs
+// use little of the GPU in their scan and frontier kernels, so there the
+// numbers run beside those instead (numbers_split_kernel: four warps per
+// tile, 32 numbers each, the last warp the rest), from the reduce pass on,
+// leaving values and tags for the build pass, joined before it.
 // `whole`: the run covers whole documents from tile 0 (not a round of a
 // chunked run), so a small parser may build the sparse table with scan 2.
-// Small whole runs give each tile four warps (32 numbers each, the last
-// warp the rest); other runs queue numbers per warp across the tiles it draws.
-static void launch_numbers(sj_parser *p, cudaStream_t s, bool whole) {
-  if (p->small && whole) {
-    sj::numbers_split_kernel<<<p->tile_blocks * 4, 128, 0, s>>>(p->d_job);
-    return;
-  }
-  sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, s>>>(p->d_job);
-}
-
 static void enqueue_stage2(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool whole, bool pdl) {
+  const bool small = p->small && whole;
   const bool sub = p->sub && whole;  // the run's s2_shift
   const Job *job = p->d_job;
+  auto numbers = [&](cudaStream_t st) {
+    if (small) sj::numbers_split_kernel<<<p->tile_blocks * 4, 128, 0, st>>>(p->d_job);
+    else sj::numbers_kernel<<<cap(p->num_grid, p->tile_blocks), 128, 0, st>>>(p->d_job);
+  };
+  auto fork_numbers = [&]() {
+    if (ev) return;
+    cudaEventRecord(p->ev_fork, s);
+    cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
+    numbers(p->aux_stream);
+    cudaEventRecord(p->ev_join, p->aux_stream);
+  };
   sj::launch_k(pdl, sub ? sj::stage2_reduce_sub_kernel : sj::stage2_reduce_kernel,
                cap(p->s2r_grid, p->tile_blocks), sj::kS2Threads, 0, s, job);
   if (ev) cudaEventRecord(ev[5], s);
-  if (!ev) {
-    cudaEventRecord(p->ev_fork, s);
-    cudaStreamWaitEvent(p->aux_stream, p->ev_fork, 0);
-    launch_numbers(p, p->aux_stream, whole);
-    cudaEventRecord(p->ev_join, p->aux_stream);
-  }
-  if (p->small && whole) {
+  if (small) {
+    fork_numbers();
     sj::launch_scan2_spt_small(job, p->spt_smem, s, pdl);  // scan, sparse table, jump pointers
   } else {
     sj::launch_scan2(job, p->scan_grid, s, pdl);
+    fork_numbers();
     for (uint32_t src = 0; src + 1 < p->spt_levels; src += 4)
       sj::launch_k(pdl, sj::spt_build_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job, src);
     sj::launch_k(pdl, sj::jump_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job);
   }
   sj::launch_k(pdl, sj::frontier_kernel, cap(p->aux_grid, p->aux_blocks), 256, 0, s, job);
   if (ev) cudaEventRecord(ev[6], s);
-  if (ev) launch_numbers(p, s, whole);
-  else cudaStreamWaitEvent(s, p->ev_join, 0);
+  if (ev) numbers(s);
   if (ev) cudaEventRecord(ev[7], s);
-  if (sub)
-    sj::stage2_build_sub_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
-  else
-    sj::stage2_build_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
-  if (ev) cudaEventRecord(ev[8], s);
+  if (small) {
+    if (!ev) cudaStreamWaitEvent(s, p->ev_join, 0);
+    if (sub) sj::stage2_build_sub_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+    else sj::stage2_build_small_kernel<<<cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s>>>(p->d_job);
+    if (ev) cudaEventRecord(ev[8], s);
+  } else {
+    sj::launch_k(pdl, sj::stage2_build_kernel, cap(p->s2b_grid, p->tile_blocks), sj::kS2Threads, 0, s, job);
+    if (ev) cudaEventRecord(ev[8], s);
+    if (!ev) cudaStreamWaitEvent(s, p->ev_join, 0);
+  }
 }
 
 // With `zc` the set-up kernel reads the run descriptor and the offsets of
@@ -448,7 +456,7 @@ static void enqueue_run(sj_parser *p, cudaStream_t s, cudaEvent_t *ev, bool zc, 
   const bool pdl = !ev;
   enqueue_stage1(p, s, ev, pdl);
   enqueue_stage2(p, s, ev, true, pdl);
-  sj::launch_k(pdl, sj::finalize_kernel, cap(p->fin_grid, p->doc_blocks), 256, 0, s, (const Job *)p->d_job);
+  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   if (ev) cudaEventRecord(ev[9], s);
 }
 
@@ -595,7 +603,7 @@ static int enqueue_chunked(sj_parser *p, const uint8_t *host, uint64_t len, cuda
     sj::chunk_range_kernel<<<1, 32, 0, s>>>(p->d_job, 0, 0, 2, c, c + 1 == nc);
     enqueue_stage2(p, s, nullptr, false, true);
   }
-  sj::launch_k(true, sj::finalize_kernel, cap(p->fin_grid, p->doc_blocks), 256, 0, s, (const Job *)p->d_job);
+  sj::finalize_kernel<<<cap(p->fin_grid, p->doc_blocks), 256, 0, s>>>(p->d_job);
   CK(cudaMemcpyAsync(p->h_results, p->d_results, sizeof(sj_doc_result), cudaMemcpyDeviceToHost, s));
   CK(cudaGetLastError());
   return SJ_SUCCESS;

@@ -12,8 +12,10 @@
 //   stage2_build_kernel   per tile: each token's enclosing container (in the
 //                         tile, found in shared memory, or from the frontier),
 //                         the grammar check against the previous two tokens
-//                         and that container, and the tape words; numbers are
-//                         converted and strings normalised into the buffer.
+//                         and that container, and the tape words; strings
+//                         are normalised into the buffer;
+//   numbers_kernel        per number: conversion and its two tape words,
+//                         beside the build pass.
 // The first failing token of a document (smallest index; grammar before
 // content at one token) gives its error code (an atomic minimum).
 #include "number.cuh"
@@ -345,7 +347,8 @@ __device__ __forceinline__ void stage2_reduce(const Job *__restrict__ job) {
                                                    : OpenTable{open_g, 0xFFFFFFFFu, kLevelOff};
     uint64_t sb = 0;  // string-buffer bytes of this lane's strings without escapes
     uint32_t shead = 0, stail = 0;
-    uint32_t nnum = 0;  // number tokens of the tile so far (listed for numbers_kernel)
+    uint32_t nnum = 0;  // number tokens of the tile so far, listed for numbers_kernel (index
+                        // and tape slot in the tile, 16 bits each)
     const uint32_t wtail0 = wtail;  // escaped strings queued before this tile
     // strings: the next 32 queued get their length from the masks; those the
     // masks cannot decide go to the walk queue
@@ -408,7 +411,7 @@ __device__ __forceinline__ void stage2_reduce(const Job *__restrict__ job) {
       enqueue(W.sq, stail, valid && kind == K_STRING, RQEntry{pos, nxt, j}, lane);
       {
         const unsigned nb = __ballot_sync(0xFFFFFFFFu, valid && kind == K_NUMBER);
-        if (valid && kind == K_NUMBER) J.nlist[ib + off + nnum + __popc(nb & ((1u << lane) - 1u))] = off + j;
+        if (valid && kind == K_NUMBER) J.nlist[ib + off + nnum + __popc(nb & ((1u << lane) - 1u))] = j | (tp << 16);
         nnum += __popc(nb);
       }
       const uint32_t tot = __shfl_sync(0xFFFFFFFFu, vi, 31);
@@ -460,19 +463,31 @@ __device__ __forceinline__ void stage2_reduce(const Job *__restrict__ job) {
 // lane per number (a tile holds too few to fill a warp).  Each lane copies its
 // lexeme and the byte after it (at most kNumWindow bytes, in 16-byte chunks)
 // into shared memory and converts it there; longer lexemes are read in place.
-// The value goes to `numv`, the tag ('l' or 'd') or the error code to the
-// token's `slen` entry.
+// numbers_kernel runs once the tile scan has given every tile its first tape
+// slot, beside the build pass, and writes the number's two tape words (tag
+// 'l' or 'd', value) itself, or reports its error.  On small whole runs
+// (numbers_split_kernel) it runs beside the tile scan instead, where a small
+// run's stage 2 leaves the GPU mostly idle, and leaves the value in `numv`
+// and the tag or error in `slen` for the build pass.
 constexpr int kNumWindow = 48;
 constexpr int kNumThreads = 128;
 struct NumEntry {
   uint64_t slot;  // the token's index slot (idx_base + index in the document)
   uint32_t d;     // its document
   uint32_t rel;   // its index in the document
+  uint32_t tp;    // its tape slot in the document
 };
+// The queue entry of number-list entry x of tile t (document d, index base ib).
+__device__ __forceinline__ NumEntry num_entry(const Job &J, uint32_t t, uint32_t d, uint64_t ib,
+                                              uint32_t off, uint32_t x) {
+  const uint32_t rel = off + (x & 0xFFFFu);
+  return NumEntry{ib + rel, d, rel, J.s2_pre[t].tape_start + (x >> 16)};
+}
 // 12 resident blocks (40 registers): the kernel waits on scattered lexeme
 // loads, so more warps in flight beat the few spilled registers.
 // One number token: its lexeme window staged in `my` (kNumWindow + 16
 // bytes of shared memory), converted; value and tag (or error) stored.
+template <bool TO_TAPE>
 __device__ __forceinline__ void convert_number(const Job &J, const NumEntry &e, uint8_t *my) {
       const uint64_t len = J.doc_off[e.d + 1] - J.doc_off[e.d];
       const uint8_t *doc = J.base + J.doc_off[e.d];
@@ -493,7 +508,16 @@ __device__ __forceinline__ void convert_number(const Job &J, const NumEntry &e, 
       } else {
         nc = parse_number(doc + pos, doc + len, tag, v);
       }
-      if (nc) {
+      if constexpr (TO_TAPE) {
+        const uint32_t tape_cap32 = (uint32_t)min(len + 3, (uint64_t)0xFFFFFFFFu);  // >= 3
+        if (nc) {
+          report(J, e.d, e.rel, nc);
+        } else if (e.tp < tape_cap32 - 1u) {
+          uint64_t *tape = J.tape + tape_base(J, e.d);
+          tape[e.tp] = (uint64_t)tag << 56;
+          tape[e.tp + 1] = v;
+        }
+      } else if (nc) {
         J.slen[e.slot] = kSlenErr | (uint32_t)nc;
       } else {
         J.slen[e.slot] = tag;
@@ -512,7 +536,7 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
   uint32_t head = 0, tail = 0;
   auto flush = [&]() {
     const uint32_t m = min(32u, tail - head);
-    if ((uint32_t)lane < m) convert_number(J, wq[(head + lane) & 63u], my);
+    if ((uint32_t)lane < m) convert_number<true>(J, wq[(head + lane) & 63u], my);
     head += m;
     __syncwarp();
   };
@@ -532,8 +556,7 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_kernel(const Job *__r
       const uint32_t k = k0 + lane;
       const uint32_t c = min(32u, m - k0);
       if ((uint32_t)lane < c) {
-        const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
-        wq[(tail + lane) & 63u] = NumEntry{ib + rel, d, rel};
+        wq[(tail + lane) & 63u] = num_entry(J, t, d, ib, off, J.nlist[ib + off + k]);
       }
       tail += c;
       __syncwarp();
@@ -569,8 +592,8 @@ __global__ void __launch_bounds__(kNumThreads, 12) numbers_split_kernel(const Jo
     const uint64_t ib = idx_base(J, d);
     const uint32_t off = J.tile_off[t];
     for (uint32_t k = k0 + lane; k < k1; k += 32) {
-      const uint32_t rel = J.nlist[ib + off + k];  // the token's index in the document
-      convert_number(J, NumEntry{ib + rel, d, rel}, my);
+      const uint32_t x = J.nlist[ib + off + k];
+      convert_number<false>(J, NumEntry{ib + off + (x & 0xFFFFu), d, off + (x & 0xFFFFu), 0u}, my);
     }
   }
 }
@@ -650,7 +673,9 @@ __device__ __forceinline__ void put_string_smem(uint8_t *__restrict__ o, uint32_
   dst[n] = 0;
 }
 
-template <uint32_t SH>
+// NUMS: the run's numbers were left in numv and slen (small whole runs), and
+// this pass writes their tape words; otherwise numbers_kernel writes them.
+template <uint32_t SH, bool NUMS>
 __device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
   const Job &J = *job;
   __shared__ BuildSmem WS[kS2Warps];
@@ -786,7 +811,7 @@ __device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
     uint64_t meta_next = (uint32_t)lane < cnt ? J.meta[ib + off + lane] : 0ull;
     uint32_t sl_next = (uint32_t)lane < cnt ? J.slen[ib + off + lane] : 0u;
     // a number's value word, loaded one chunk ahead once the kinds are known
-    uint64_t nv_next = ((uint32_t)lane < cnt && (meta_next & 15u) == K_NUMBER)
+    uint64_t nv_next = (NUMS && (uint32_t)lane < cnt && (meta_next & 15u) == K_NUMBER)
                            ? J.numv[ib + off + lane] : 0ull;
     // kinds of the two tokens before the tile
     uint8_t prev1 = K_OTHER, prev2 = K_OTHER;
@@ -862,13 +887,15 @@ __device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
             tape[tp] = ((uint64_t)(k == K_CLOSE_OBJ ? '}' : ']') << 56) | par_tape;
             tape[par_tape] = ((uint64_t)(k == K_CLOSE_OBJ ? '{' : '[') << 56) | (uint64_t)(tp + 1);
           }
-        } else if (k == K_NUMBER) {  // converted by the reduce pass (Sec. 3.2.1)
-          if (sl_all & kSlenErr) {
-            if (!code) code = (int)(sl_all & 0xFFu);
-          } else if (tp < tape_cap32 - 1u) {  // tape_cap32 >= 3
-            tape[tp] = (uint64_t)(sl_all & 0xFFu) << 56;
-            tape[tp + 1] = nv;
-          }
+        } else if (k == K_NUMBER) {
+          if constexpr (NUMS) {  // converted by numbers_split_kernel (Sec. 3.2.1)
+            if (sl_all & kSlenErr) {
+              if (!code) code = (int)(sl_all & 0xFFu);
+            } else if (tp < tape_cap32 - 1u) {  // tape_cap32 >= 3
+              tape[tp] = (uint64_t)(sl_all & 0xFFu) << 56;
+              tape[tp + 1] = nv;
+            }
+          }  // else numbers_kernel writes the words
         } else if (is_atom(k)) {
           // the literal and the byte after it: one 8-byte window of the staged
           // tile (two aligned words and a funnel shift), else byte by byte
@@ -895,7 +922,8 @@ __device__ __forceinline__ void stage2_build(const Job *__restrict__ job) {
         if (code) report(J, d, g, code);
       }
       enqueue(W.sq, stail, valid && k == K_STRING, QEntry{pos, nxt, j, trel, sl}, lane);
-      nv_next = (j + 32 < cnt && (meta_next & 15u) == K_NUMBER) ? J.numv[ib + off + j + 32] : 0ull;
+      if constexpr (NUMS)
+        nv_next = (j + 32 < cnt && (meta_next & 15u) == K_NUMBER) ? J.numv[ib + off + j + 32] : 0ull;
       __syncwarp();
       if (stail - shead >= 32) flush_strings();
     }
@@ -1062,11 +1090,15 @@ __global__ void __launch_bounds__(kS2Threads, 7) stage2_reduce_sub_kernel(const 
 }
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_kernel(const Job *__restrict__ job) {
   pdl_enter();
-  stage2_build<0>(job);
+  stage2_build<0, false>(job);
+}
+__global__ void __launch_bounds__(kS2Threads, 7) stage2_build_small_kernel(const Job *__restrict__ job) {
+  pdl_enter();
+  stage2_build<0, true>(job);
 }
 __global__ void __launch_bounds__(kS2Threads, 7) stage2_build_sub_kernel(const Job *__restrict__ job) {
   pdl_enter();
-  stage2_build<kSmallShift>(job);
+  stage2_build<kSmallShift, true>(job);
 }
 
 }  // namespace sj

@@ -139,8 +139,9 @@ struct Job {
   uint32_t *slen;           // per index slot: normalised length of the string token there
   uint64_t *meta;           // per index slot: token facts from the stage-2 reduce pass
   uint8_t *unesc;           // per input byte: normalised strings with escapes, at their position
-  uint64_t *numv;           // per index slot: the value word of a number token
-  uint32_t *nlist;          // per index slot: the number tokens of each tile, listed from its first slot
+  uint32_t *nlist;          // per index slot: the number tokens of each tile, listed from its
+                            // first slot (index and tape slot in the tile, 16 bits each)
+  uint64_t *numv;           // per index slot: a number's value word (small whole runs only)
   uint32_t *tile_nnum;      // per tile: number tokens
   uint16_t *open_g;         // per stage-2 reduce warp: level table for tiles with many tokens
   uint64_t *front;          // per index slot + tile: open container of each level entering a tile
