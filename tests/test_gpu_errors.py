@@ -1,7 +1,10 @@
 """GPU parity on the error-category families of test_oracle_errors: documents
 with one injected defect, and with two ordered defects, parsed one by one and
 as one batch; error codes and, where the oracle compares them, indices are
-those of the oracle."""
+those of the oracle.  Each runs on a parser sized to the documents (at most
+2048 stage-2 tiles: numbers converted beside the tile scans, their tape
+words written by the build pass) and on a 16 MiB one (numbers converted
+beside the build pass, which write their own tape words and errors)."""
 import random
 import zlib
 
@@ -16,7 +19,10 @@ pytestmark = pytest.mark.gpu
 
 PAIRS = [(("value", b"tru"), ("value", b"1.")), (("value", b"1."), ("value", b"tru")),
          (("string", b"\\q"), ("value", b"nul")), (("string", b"a\x02"), ("string", b"\\q")),
-         (("value", b"tru"), ("string", b"\xff")), (("value", b"1 2"), ("value", b"fals"))]
+         (("value", b"tru"), ("string", b"\xff")), (("value", b"1 2"), ("value", b"fals")),
+         # a grammar error and a number error at one token: the grammar's code
+         (("value", b"1 2."), ("value", b"nul"))]
+BIG = 16 << 20  # a parser above 2048 stage-2 tiles
 
 
 @pytest.fixture(scope="module")
@@ -31,9 +37,10 @@ def docs():
     return out
 
 
-def test_defect_documents_one_by_one(docs):
+@pytest.mark.parametrize("big", [False, True])
+def test_defect_documents_one_by_one(docs, big):
     import paper_1902_08318_gb300 as sj
-    p = sj.Parser(max_bytes=max(len(d) for d in docs) + 64)
+    p = sj.Parser(max_bytes=max(max(len(d) for d in docs) + 64, BIG if big else 0))
     try:
         for i, d in enumerate(docs):
             gpuutil.check_doc(p, d, f"doc {i}")
@@ -41,10 +48,11 @@ def test_defect_documents_one_by_one(docs):
         p.close()
 
 
-def test_defect_documents_in_one_batch(docs):
+@pytest.mark.parametrize("big", [False, True])
+def test_defect_documents_in_one_batch(docs, big):
     import paper_1902_08318_gb300 as sj
     buf, off = gpuutil.batch_arrays(docs)
-    p = sj.Parser(max_bytes=int(off[-1]) + 64, max_docs=len(docs))
+    p = sj.Parser(max_bytes=max(int(off[-1]) + 64, BIG if big else 0), max_docs=len(docs))
     try:
         res, ptrs = p.parse_batch(buf, off)
         exp = oracle.parse_many_errors(buf, off)
