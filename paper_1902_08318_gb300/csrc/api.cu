@@ -302,7 +302,11 @@ static int create_impl(sj_parser *p, uint64_t max_bytes, uint32_t max_docs, uint
   CK(cudaMemset(p->d_open_g, 0, open_entries * sizeof(uint16_t)));
   int occn = 0;
   CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occn, sj::numbers_kernel, 128, 0));
-  p->num_grid = sms * (occn > 0 ? occn : 1);
+  // half its occupancy: the numbers kernel runs beside the build pass, and at
+  // full occupancy its blocks, launched first, hold the build's off the SMs
+  // (1 GiB document: 12 blocks per SM 8.56 ms, 6 blocks 8.50, 4 blocks 8.60,
+  // 2 blocks 8.72)
+  p->num_grid = sms * (occn > 1 ? occn / 2 : 1);
   p->fin_grid = sms * 4;
   p->aux_grid = sms * 8;
   p->tile_blocks = (int)((tiles2 + 3) / 4);
