@@ -5,7 +5,8 @@ the paper fixes (Sec. 3, Sec. 3.1.5, Sec. 3.2.1, Sec. 3.2.2; the precedence
 of several problems is the reading listed with the oracle), and the oracle
 must give that category.  With two defects, the precedence decides: a UTF-8
 error or an unclosed string before any token error, else the first failing
-token in document order."""
+token in document order; inside one token, a grammar failure before a content
+failure, and inside one string the first problem in byte order."""
 import json
 import random
 import zlib
@@ -132,3 +133,33 @@ def test_unclosed_string_before_token_errors():
         d = _two(rng, ("value", b"tru"), ("value", b"1."))
         assert oracle.parse(d + b'"')["error"] == oracle.UNCLOSED_STRING
         assert oracle.parse(d + b'"\xff')["error"] == oracle.UTF8_ERROR
+
+
+# Problems inside one token, with the category the readings fix: a grammar
+# failure at a token comes before a content failure of the same token, and
+# inside one string the first problem in byte order decides.
+SAME_TOKEN = [
+    (b"[1 2.]", oracle.TAPE_ERROR),            # no comma before a bad number
+    (b'{"a" tru}', oracle.TAPE_ERROR),         # no colon before a bad atom
+    (b'["a" "\\q"]', oracle.TAPE_ERROR),       # no comma before a bad escape
+    (b'{"a":1 "b\\q":2}', oracle.TAPE_ERROR),  # no comma before a key with a bad escape
+    (b'["\\q\x01"]', oracle.STRING_ERROR),     # bad escape, then a control byte
+    (b'["\x01\\q"]', oracle.UNESCAPED_CHARS),  # control byte, then a bad escape
+    (b'["\\ud800\x02"]', oracle.STRING_ERROR),  # lone surrogate, then a control byte
+    (b'["a\x1f\\ud800"]', oracle.UNESCAPED_CHARS),
+]
+
+
+@pytest.mark.parametrize("doc,code", SAME_TOKEN)
+def test_problems_inside_one_token(doc, code):
+    assert oracle.parse(doc)["error"] == code
+
+
+@pytest.mark.parametrize("doc,code", [c for c in SAME_TOKEN if c[0].startswith(b"[")])
+def test_problems_inside_one_token_in_records(doc, code):
+    # the same array, as a value inside a seeded valid document, keeps its category
+    rng = random.Random(zlib.crc32(doc))
+    inner = doc[1:-1]  # the array's content
+    for _ in range(10):
+        d = _doc_with(rng, VAL_MARK).replace(str(VAL_MARK).encode(), b"[" + inner + b"]", 1)
+        assert oracle.parse(d)["error"] == code, d[:200]
