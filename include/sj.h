@@ -246,7 +246,8 @@ sj_status sj_parser_prepare(sj_parser *p, uint32_t max_docs);
  * the two stages can be interleaved over a stream of chunks).  Results are
  * identical to a parse of the same bytes in device memory.  chunk_bytes is
  * the largest chunk, rounded up to a multiple of 2048: the first chunk is
- * 1/16 of it and each next one doubles up to it; at most 64 chunks, the last
+ * 1/16 of it and each next one 7/4 of the one before, up to it (the host link
+ * copies about 1.75 times as fast as the kernels parse); at most 64 chunks, the last
  * taking what remains.  0 turns chunking off (stage 1 then reads the pinned
  * document over the host link itself); the default is 512 MiB.  Such runs
  * launch their kernels directly (no graph; about 20 launches per chunk) and
