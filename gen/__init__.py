@@ -15,7 +15,8 @@ Workloads (stand-ins for the paper's files, which are not reproduced):
            polygons of 50-300 [lon, lat] pairs with 15-17 significant digits,
            1% in exponent form, minimal white space (canada.json stand-in).
   config2  single large document (default 1 GiB): a root array of config0-style
-           records, ~30% of string bytes non-ASCII (2/3/4-byte scalars 5:3:2),
+           records, ~26% of the bytes of string values non-ASCII (2/3/4-byte
+           scalars 5:3:2; keys stay ASCII),
            \\u surrogate pairs, long strings and escape runs placed on 64 B,
            2 KiB and 128 KiB edges, 1% of records nested to depth 1024.
   config3  batch of documents from the config0 generator with log-normal sizes
@@ -40,7 +41,7 @@ _SO = os.path.join(_HERE, "_build", "libsjgen.so")
 _lock = threading.Lock()
 _lib = None
 
-NONASCII_P = 0.137  # per string character; gives ~30% of string bytes non-ASCII at 2.7 B/char
+NONASCII_P = 0.137  # per character of a string value: ~26% of their bytes non-ASCII
 
 
 def build(force: bool = False) -> str:

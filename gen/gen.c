@@ -310,24 +310,32 @@ uint64_t sjg_records(uint64_t seed, uint64_t target, int root_array, int pretty,
   return w.overflow ? 0 : w.n;
 }
 
-/* A coordinate with 15..17 significant digits, |value| <= lim; 1% in exponent form. */
-static void emit_coord(wbuf *w, rng_t *r, int lim_digits, int lim) {
+/* A coordinate: an integer part uniform in [-(lim - 1), lim - 1] and random
+ * fraction digits up to 15..17 significant digits, so |value| < lim; 1% are
+ * written in exponent form (the same digits with one before the point and
+ * the exponent moving the point back; a value below 1 keeps the plain form). */
+static void emit_coord(wbuf *w, rng_t *r, int lim) {
   int sig = (int)rrange(r, 15, 17);
-  int64_t ipart = rrange(r, -lim, lim);
-  if (runif(r) < 0.01) {
-    if (ipart < 0) put(w, '-');
-    emit_decimal(w, r, sig, 1, (int)rrange(r, -3, 2), 1);
-    return;
-  }
+  int64_t ipart = rrange(r, -(lim - 1), lim - 1);
+  const int expo_form = runif(r) < 0.01;
   uint64_t m = ipart < 0 ? (uint64_t)(-ipart) : (uint64_t)ipart;
   if (ipart < 0 || (ipart == 0 && runif(r) < 0.5)) put(w, '-');
   char tmp[8]; int k = 0;
   do { tmp[k++] = (char)('0' + m % 10); m /= 10; } while (m);
   int ip_digits = (ipart == 0) ? 0 : k;
+  if (expo_form && ip_digits > 0) {
+    put(w, (uint8_t)tmp[--k]);
+    put(w, '.');
+    while (k) put(w, (uint8_t)tmp[--k]);
+    emit_digits(w, r, sig - ip_digits, 0);
+    put(w, runif(r) < 0.5 ? 'e' : 'E');
+    if (runif(r) < 0.5) put(w, '+');
+    put(w, (uint8_t)('0' + (ip_digits - 1)));
+    return;
+  }
   while (k) put(w, (uint8_t)tmp[--k]);
   put(w, '.');
   emit_digits(w, r, sig - ip_digits, 0);
-  (void)lim_digits;
 }
 
 /* Number-heavy GeoJSON-like document: an object wrapping an array of polygons,
@@ -345,9 +353,9 @@ uint64_t sjg_geo(uint64_t seed, uint64_t target, uint8_t *out, uint64_t cap) {
     for (int i = 0; i < pairs; i++) {
       if (i) put(&w, ',');
       put(&w, '[');
-      emit_coord(&w, &r, 3, 180);
+      emit_coord(&w, &r, 180);
       put(&w, ',');
-      emit_coord(&w, &r, 2, 90);
+      emit_coord(&w, &r, 90);
       put(&w, ']');
     }
     put(&w, ']');
